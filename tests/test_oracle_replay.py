@@ -1,0 +1,267 @@
+"""Pins for the oracle's order replay (CPU only).
+
+The replay is pinned against a second, independent composition of the same
+documented order written here in Python: each chain's pair comes from the
+paper's sequential loop (Example 1 / Example 3 / the direct and the
+double-accumulator loops, or their TwoProduct dot forms) run on the chain's
+subsequence, and the tree / butterfly / grid folds are composed from the
+oracle's TWO-SUM (Theorem 2).  Special cases then tie the replay to the exact
+oracle: integer data, n = 0 and n = 1, sign symmetry, and the error bound of
+the rigorous variant with the tree's dependency depth D in place of n - 1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1401_0248_gb300 import inputs as I
+
+LOOP = {("sum", "plain"): "sum", ("sum", "fast"): "sumtf", ("sum", "rigorous"): "sumt",
+        ("sum", "wide"): "sumd", ("dot", "plain"): "dot", ("dot", "fast"): "dottf2",
+        ("dot", "rigorous"): "dott2", ("dot", "wide"): "dotd"}
+
+
+class Arith:
+    def __init__(self, f32, twofold):
+        self.t = np.float32 if f32 else np.float64
+        self.twofold = twofold
+
+    def merge(self, a, b):
+        if not self.twofold:
+            return (self.t(self.t(a[0]) + self.t(b[0])), self.t(0))
+        x, y = O.two_sum(np.array([a[0]], self.t), np.array([b[0]], self.t))
+        e = self.t(self.t(self.t(a[1]) + self.t(b[1])) + y[0])
+        return (x[0], e)
+
+    def butterfly(self, vals):
+        v = list(vals)
+        W = len(v)
+        o = W // 2
+        while o >= 1:
+            v = [self.merge(v[i], v[i ^ o]) for i in range(W)]
+            o //= 2
+        return v[0]
+
+    def tree(self, ch):
+        ch = list(ch)
+        w = len(ch) // 2
+        while w >= 1:
+            for c in range(w):
+                ch[c] = self.merge(ch[c], ch[c + w])
+            w //= 2
+        return ch[0]
+
+
+def chain_pair(op, variant, x, y, idx):
+    m = LOOP[(op, variant)]
+    if len(idx) == 0:
+        return (0.0, 0.0)
+    xs = x[idx]
+    ys = None if y is None else y[idx]
+    v, e = O.loop(m, xs, ys)
+    return (v, e)
+
+
+def out_pair(dt, variant, r, out_f64):
+    if dt == np.float64 or out_f64:
+        return np.array([r[0], r[1]], dtype=np.float64)
+    if variant == "plain":
+        return np.array([r[0], r[1]], dtype=np.float32)
+    v = np.float32(r[0])
+    d = (np.float64(r[0]) - np.float64(v)) + np.float64(r[1])
+    return np.array([v, np.float32(d)], dtype=np.float32)
+
+
+def compose_flat(op, variant, x, y, block, unroll, grid, out_f64=False):
+    dt = x.dtype.type
+    f32 = dt == np.float32
+    V = 4 if f32 else 2
+    n = x.size
+    nv, tail = n // V, n % V
+    P = grid * block
+    tw = variant in ("fast", "rigorous")
+    ab = Arith(f32 and variant != "wide", tw)
+    ag = Arith(f32 and variant == "plain", tw)
+    C = unroll * V
+    bps = []
+    for b in range(grid):
+        tps = []
+        for t in range(block):
+            g = b * block + t
+            lists = [[] for _ in range(C)]
+            m = 0
+            while g + P * m < nv:
+                j = g + P * m
+                for l in range(V):
+                    lists[(m % unroll) * V + l].append(j * V + l)
+                m += 1
+            if tail and g == nv % P:
+                m = nv // P
+                for l in range(tail):
+                    lists[(m % unroll) * V + l].append(nv * V + l)
+            ch = [chain_pair(op, variant, x, y, np.array(li, dtype=np.int64)) for li in lists]
+            tps.append(ab.tree(ch))
+        wps = [ab.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
+        bps.append(ab.butterfly(wps))
+    tps = []
+    for t in range(block):
+        a = (0.0, 0.0)
+        if t < grid:
+            a = bps[t]
+            for i in range(t + block, grid, block):
+                a = ag.merge(a, bps[i])
+        tps.append(a)
+    wps = [ag.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
+    return out_pair(dt, variant, ag.butterfly(wps), out_f64)
+
+
+CASES = [
+    ("sum", "fast", np.float32, 1000, 32, 1, 2),
+    ("sum", "rigorous", np.float32, 4099, 64, 2, 3),
+    ("sum", "plain", np.float32, 777, 32, 2, 1),
+    ("sum", "wide", np.float32, 1501, 64, 1, 2),
+    ("dot", "fast", np.float32, 2003, 32, 2, 2),
+    ("dot", "rigorous", np.float64, 1999, 64, 1, 3),
+    ("dot", "plain", np.float64, 901, 32, 1, 2),
+    ("dot", "wide", np.float32, 1203, 32, 4, 1),
+    ("sum", "fast", np.float64, 3001, 32, 4, 5),
+    ("sum", "rigorous", np.float64, 2500, 64, 2, 2),
+]
+
+
+@pytest.mark.parametrize("op,variant,dt,n,block,unroll,grid", CASES)
+@pytest.mark.parametrize("out_f64", [False, True])
+def test_replay_flat_matches_composition(op, variant, dt, n, block, unroll, grid, out_f64):
+    s = "f32" if dt == np.float32 else "f64"
+    x = I.normal(n, s, seed=n % 4096).numpy()
+    y = I.normal(n, s, seed=n % 4096, stream=4).numpy() if op == "dot" else None
+    want = compose_flat(op, variant, x, y, block, unroll, grid, out_f64)
+    got = O.replay_flat(op, variant, x, y, block=block, unroll=unroll, grid=grid, out_f64=out_f64)
+    assert got.dtype == want.dtype
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (got, want)
+
+
+def test_replay_special_cases():
+    for dt in ("f32", "f64"):
+        x = I.normal(1, dt, seed=1).numpy()
+        for variant in ("plain", "fast", "rigorous"):
+            got = O.replay_flat("sum", variant, x, block=256, unroll=4, grid=7)
+            assert got[0] == x[0] and got[1] == 0
+            got = O.replay_flat("sum", variant, x[:0], block=256, unroll=4, grid=7)
+            assert got[0] == 0 and got[1] == 0 and not np.signbit(got[0])
+    rng = np.random.default_rng(2)
+    xi = rng.integers(-100, 100, size=100003).astype(np.float32)
+    S = float(np.sum(xi.astype(np.int64)))
+    for variant in ("plain", "fast", "rigorous", "wide"):
+        got = O.replay_flat("sum", variant, xi, block=128, unroll=2, grid=9)
+        assert float(got[0]) == S and got[1] == 0
+    x = I.normal(5001, "f64", seed=3).numpy()
+    a = O.replay_flat("sum", "rigorous", x, block=64, unroll=2, grid=4)
+    b = O.replay_flat("sum", "rigorous", -x, block=64, unroll=2, grid=4)
+    assert a[0] == -b[0] and a[1] == -b[1]
+
+
+def depth(n, V, block, unroll, grid):
+    per_thread = math.ceil(n / (V * grid * block))
+    return (per_thread + int(math.log2(unroll * V)) + 5 + int(math.log2(block // 32))
+            + math.ceil(math.log2(max(grid, 2))) + 5 + int(math.log2(block // 32)))
+
+
+@pytest.mark.parametrize("dt,cond", [("f32", 1e4), ("f64", 1e12)])
+def test_replay_rigorous_bound_with_tree_depth(dt, cond):
+    n = 1 << 17
+    ic = I.ill_conditioned(n, dt, cond, seed=21)
+    x = ic.x.numpy()
+    u = 2.0 ** -24 if dt == "f32" else 2.0 ** -53
+    V = 4 if dt == "f32" else 2
+    block, unroll, grid = 128, 2, 16
+    got = O.replay_flat("sum", "rigorous", x, block=block, unroll=unroll, grid=grid, out_f64=True)
+    r = O.exact(x, v=float(got[0]), e=float(got[1]))
+    D = depth(n, V, block, unroll, grid)
+    g = D * u / (1 - D * u)
+    assert abs(r.r) <= u * abs(r.s) + g * g * r.sabs
+
+
+# ------------------------------------------------------------------- CSR
+def compose_csr(op, variant, x, y, off, unroll, tile, out_f64=False):
+    dt = x.dtype.type
+    f32 = dt == np.float32
+    V = 4 if f32 else 2
+    tw = variant in ("fast", "rigorous")
+    ab = Arith(f32 and variant != "wide", tw)
+    ag = Arith(f32 and variant == "plain", tw)
+    C = unroll * V
+    outs = []
+    for s in range(off.size - 1):
+        a, b = int(off[s]), int(off[s + 1])
+        if a == b:
+            outs.append(out_pair(dt, variant, (0.0, 0.0), out_f64))
+            continue
+        pcs = []
+        for w in range(a // tile, (b - 1) // tile + 1):
+            lo, hi = max(a, w * tile), min(b, (w + 1) * tile)
+            lists = [[[] for _ in range(C)] for _ in range(32)]
+            for i in range(lo, hi):
+                r = i - w * tile
+                q = r // V
+                lists[q % 32][((q // 32) % unroll) * V + r % V].append(i)
+            lanes = [ab.tree([chain_pair(op, variant, x, y, np.array(li, dtype=np.int64))
+                              for li in lists[l]]) for l in range(32)]
+            pcs.append(ab.butterfly(lanes))
+        if len(pcs) == 1:
+            res = pcs[0]
+        else:
+            lanes = []
+            for l in range(32):
+                acc = (0.0, 0.0)
+                if l < len(pcs):
+                    acc = pcs[l]
+                    for i in range(l + 32, len(pcs), 32):
+                        acc = ag.merge(acc, pcs[i])
+                lanes.append(acc)
+            res = ag.butterfly(lanes)
+        outs.append(out_pair(dt, variant, res, out_f64))
+    return np.array(outs)
+
+
+@pytest.mark.parametrize("op,variant,dt,unroll,tile", [
+    ("sum", "fast", np.float32, 1, 128), ("sum", "rigorous", np.float64, 2, 128),
+    ("dot", "fast", np.float64, 1, 64), ("dot", "rigorous", np.float32, 2, 256),
+    ("sum", "plain", np.float32, 1, 128), ("dot", "wide", np.float32, 1, 128),
+])
+def test_replay_csr_matches_composition(op, variant, dt, unroll, tile):
+    s = "f32" if dt == np.float32 else "f64"
+    L = I.csr_lengths(24, 1, 700, seed=5)
+    L[3] = 0
+    L[10] = 0
+    off = I.csr_offsets(L)
+    n = int(off[-1])
+    x = I.normal(n, s, seed=6).numpy()
+    y = I.normal(n, s, seed=6, stream=2).numpy() if op == "dot" else None
+    want = compose_csr(op, variant, x, y, off, unroll, tile)
+    got = O.replay_csr(op, variant, x, off, y, unroll=unroll, tile=tile, nthreads=3)
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+
+
+def test_replay_csr_segments_independent_and_empty():
+    L = I.csr_lengths(50, 1, 5000, seed=7)
+    off = I.csr_offsets(L)
+    x = I.normal(int(off[-1]), "f32", seed=8).numpy()
+    a = O.replay_csr("sum", "rigorous", x, off, unroll=2, tile=1024)
+    # insert empty segments everywhere: the non-empty results do not change
+    off2 = np.repeat(off, 2)[1:-1]
+    off2 = np.concatenate([[0], off2, [off[-1]]])
+    b = O.replay_csr("sum", "rigorous", x, off2, unroll=2, tile=1024)
+    nonempty = np.diff(off2) > 0
+    assert np.array_equal(b[nonempty], a)
+    assert np.all(b[~nonempty] == 0)
+    # one segment that is the whole vector: the bound holds with tile depth
+    ic = I.ill_conditioned(1 << 16, "f64", 1e10, seed=9)
+    xx = ic.x.numpy()
+    got = O.replay_csr("sum", "rigorous", xx, np.array([0, xx.size]), unroll=2, tile=512)[0]
+    r = O.exact(xx, v=float(got[0]), e=float(got[1]))
+    u = 2.0 ** -53
+    D = 512 // 64 + 2 + 5 + (xx.size // 512) // 32 + 5
+    g = D * u / (1 - D * u)
+    assert abs(r.r) <= u * abs(r.s) + g * g * r.sabs
