@@ -1,0 +1,572 @@
+"""Benchmark: twofold sum / dot on GB300 -- GB/s and relative error vs exact.
+
+Workload (the benchmark's headline configuration): single vectors of
+N = 2^28 elements, binary32 and binary64, twofold sum and dot with the fast
+(Dekker) and rigorous (Knuth) variants, on ill-conditioned data with target
+condition numbers 1e4, 1e8 and 1e16 (half the entries with exponents spread
+over 0..E, the rest cancelling them, seeded synthetic data).  One step is one
+pass of all 24 twofold reductions (2 dtypes x 2 ops x 2 variants x 3
+condition numbers).  Plain binary32/binary64 sums and dots and the binary64
+accumulator ('wide', binary32 data) run alongside on the same data and are
+reported per kernel, not in the step.
+
+value    whole-step algorithmic bytes / device time (CUDA events, inputs
+         resident in HBM, every input larger than L2).
+e2e      the same step through the C ABI's host-buffer calls: pinned host
+         inputs copied to the device inside the timed region, the result pair
+         copied back.
+roofline the kernel with the largest share of the step time, against the
+         measured HBM copy bandwidth or, for binary64 kernels bound by the
+         binary64 pipe, against the binary64 instruction peak.
+cpu_baseline  the CPU oracle's sequential loops (the paper's twofold loops)
+         timed on a bounded sample of the same workload on one host core.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) each rank reduces its own copy of the workload (the
+path shards into independent problems, no collective on the data path); the
+step time is the maximum over ranks and value counts all ranks' bytes.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from fractions import Fraction
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GB/s & rel. error vs exact: twofold vs plain sum/dot, same GB300"
+CONDS = (1e4, 1e8, 1e16)
+OPS = ("sum", "dot")
+TWOFOLD = ("fast", "rigorous")
+N_DEFAULT = 1 << 28
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+PLANS_PATH = os.path.join(ROOT, "paper_1401_0248_gb300", "plans_gb300.txt")
+FALLBACK_HBM_GBS = 6800.0
+FP64_INSTR_PER_CLK_PER_SM = 2.0       # 1.25 TFLOP/s FP64 (FMA = 2 flops) at 2070 MHz, 152 SMs
+
+# FP64-pipe instructions per element of each binary64 kernel (sum: add/sub
+# counts of Examples 1 and 3; dot: + multiply + fma (TwoProduct) + 1)
+FP64_OPS = {("sum", "plain"): 1, ("sum", "fast"): 4, ("sum", "rigorous"): 7,
+            ("dot", "plain"): 2, ("dot", "fast"): 7, ("dot", "rigorous"): 10}
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1401_0248_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------- distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = os.environ.get("TF_BENCH_BACKEND", "nccl")
+    if backend == "nccl":
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def max_over_ranks(value, world):
+    """max of a float over all ranks (identity at world size 1)"""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, world):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, enabled=True):
+        self.index = index
+        self.enabled = enabled
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workload
+def build_workload(n, device, seed=0, conds=CONDS):
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    data = {}
+    for dt in ("f32", "f64"):
+        for cond in conds:
+            s = I.ill_conditioned(n, dt, cond, seed=seed, device=device)
+            d = I.ill_conditioned(n, dt, cond, seed=seed + 1, device=device, dot=True)
+            data[(dt, cond)] = {"sum": (s.x, None, s.S, s.cond), "dot": (d.x, d.y, d.S, d.cond)}
+    torch.cuda.synchronize()
+    return data
+
+
+def kernel_list(include_baselines, conds=CONDS, only=None):
+    """(dtype, cond, op, variant, in_step) of every launch; `only` keeps the
+    named kernels ("f64_dot_rigorous", ...) for profiling runs."""
+    ks = []
+    for dt in ("f32", "f64"):
+        for cond in conds:
+            for op in OPS:
+                for v in TWOFOLD:
+                    ks.append((dt, cond, op, v, True))
+                if include_baselines:
+                    ks.append((dt, cond, op, "plain", False))
+                    if dt == "f32":
+                        ks.append((dt, cond, op, "wide", False))
+    if only:
+        ks = [k for k in ks if "%s_%s_%s" % (k[0], k[2], k[3]) in only]
+        ks = [(a, b, c, d, True) for a, b, c, d, _ in ks]
+    return ks
+
+
+def nbytes(dt, op, n):
+    return n * (4 if dt == "f32" else 8) * (2 if op == "dot" else 1)
+
+
+def rel_err(S, v, e=0.0):
+    if S == 0:
+        return None
+    approx = Fraction(float(v)) + Fraction(float(e))
+    return float(abs(S - approx) / abs(S))
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if os.path.exists(PLANS_PATH):
+        tf.plan_load(PLANS_PATH)
+    n = args.n
+    data = build_workload(n, dev, seed=rank, conds=args.conds)
+    ks_all = kernel_list(True, args.conds, args.only)
+    step_ks = [k for k in ks_all if k[4]]
+    wsz = max(tf.workspace_size(op, False, torch.float32 if dt == "f32" else torch.float64, v, n)
+              for dt, _, op, v, _ in ks_all)
+    ws = torch.zeros(wsz, dtype=torch.uint8, device=dev)
+    outs = {k: torch.empty(2, dtype=torch.float32 if k[0] == "f32" else torch.float64, device=dev)
+            for k in ks_all}
+    stream = torch.cuda.current_stream(dev)
+
+    def launch(k):
+        dt, cond, op, v, _ = k
+        x, y, _, _ = data[(dt, cond)][op]
+        if op == "sum":
+            tf.sum(x, v, out=outs[k], ws=ws)
+        else:
+            tf.dot(x, y, v, out=outs[k], ws=ws)
+
+    # warm-up steps (also loads the kernels)
+    for _ in range(args.warmup):
+        for k in ks_all:
+            launch(k)
+    torch.cuda.synchronize()
+
+    # timed steps: events around each launch on the launching stream
+    ev = {k: [] for k in step_ks}
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local, enabled=not args.no_clocks) as clk:
+        t_wait = time.perf_counter() + (0.5 if not args.no_clocks else 0.0)
+        while time.perf_counter() < t_wait:          # let the sampler start under load
+            launch(step_ks[-1])
+            torch.cuda.synchronize()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            for k in step_ks:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                launch(k)
+                b.record(stream)
+                ev[k].append((a, b))
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    step_ms_local = t_start.elapsed_time(t_end) / args.steps
+    step_ms = max_over_ranks(step_ms_local, world)
+    clocks = clk.summary()
+    kern_ms = {k: sum(a.elapsed_time(b) for a, b in ev[k]) / len(ev[k]) for k in step_ks}
+
+    # baselines alongside (plain, wide): timed the same way, outside the step
+    base_ms = {}
+    for k in [k for k in ks_all if not k[4]]:
+        for _ in range(2):
+            launch(k)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        reps = max(3, args.steps)
+        a.record(stream)
+        for _ in range(reps):
+            launch(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        base_ms[k] = a.elapsed_time(b) / reps
+
+    probes = None if args.no_probes else run_probes(data, dev, stream, args.conds[0])
+
+    step_bytes = sum(nbytes(k[0], k[2], n) for k in step_ks)
+    total_bytes = sum_over_ranks(step_bytes, world)
+    value = total_bytes / (step_ms * 1e-3) / 1e9
+
+    # per-kernel report and accuracy
+    hbm, peak_kind = load_peaks()
+    kernels, accuracy = {}, {}
+    for k in ks_all:
+        dt, cond, op, v, _ = k
+        ms = kern_ms.get(k, base_ms.get(k))
+        gbs = nbytes(dt, op, n) / (ms * 1e-3) / 1e9
+        name = "%s_%s_%s_c%g" % (dt, op, v, cond)
+        kernels[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4)}
+        _, _, S, cond_got = data[(dt, cond)][op]
+        o = outs[k].cpu().tolist()
+        acc = {"cond": float("%.3g" % cond_got), "rel_err_v_plus_e": rel_err(S, o[0], o[1]),
+               "rel_err_v": rel_err(S, o[0])}
+        if v in TWOFOLD:
+            rv = S - Fraction(float(o[0]))
+            acc["e_over_residual"] = (float(Fraction(float(o[1])) / rv) if rv != 0 else None)
+        accuracy[name] = acc
+
+    # roofline of the kernel with the largest share of the step
+    dom = max(step_ks, key=lambda k: kern_ms[k])
+    dt, cond, op, v, _ = dom
+    dom_name = "%s_%s_%s" % (dt, op, v)
+    dom_ms = statistics.mean(kern_ms[k] for k in step_ks if k[0] == dt and k[2] == op and k[3] == v)
+    traffic = None
+    try:
+        with open(TRAFFIC_PATH) as f:
+            tr = json.load(f)
+        ent = tr.get("kernels", {}).get(dom_name)
+        if ent and tr.get("sources_hash") == kernel_sources_hash() and ent.get("n") == n:
+            traffic = ent["dram_bytes"]
+    except Exception:
+        pass
+    bytes_dom = nbytes(dt, op, n)
+    if dt == "f64":
+        mhz = clocks.get("sm_mhz") or 2070.0
+        sms = tf.sm_count()
+        peak_ops = FP64_INSTR_PER_CLK_PER_SM * sms * mhz * 1e6 / 1e9      # G FP64 instr/s
+        ops = FP64_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": round(ops, 1), "peak": round(peak_ops, 1),
+                    "unit": "G fp64-instr/s", "frac": round(ops / peak_ops, 4), "traffic": traffic,
+                    "kernel": dom_name, "peak_source": "2 FP64 instr/clk/SM x SMs x median SM clock",
+                    "hbm_gbs": round(bytes_dom / (dom_ms * 1e-3) / 1e9, 1),
+                    "hbm_frac": round(bytes_dom / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
+    else:
+        ach = bytes_dom / (dom_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(ach / hbm, 4), "traffic": traffic, "kernel": dom_name,
+                    "peak_source": peak_kind}
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded SplitMix64; ill-conditioned, exact sum known by construction)",
+        "config": {"workload": "single vectors N=2^28, f32+f64, twofold sum+dot, fast+rigorous, "
+                               "cond 1e4/1e8/1e16 (24 reductions per step)",
+                   "n": n, "conds": list(args.conds), "l2": "inputs larger than L2 (1-4 GiB each)",
+                   "subset": sorted(args.only) or None,
+                   "parallelism": "replicas" if world == 1 else "independent problems per rank"},
+        "gpu_launches": len(step_ks) * args.steps,
+        "clocks": clocks,
+        "roofline": roofline,
+        "kernels": kernels,
+        "accuracy": accuracy,
+        "probes": probes,
+    }
+    return result, data, ws, outs, ks_all, step_ks
+
+
+def run_probes(data, dev, stream, cond0):
+    """Read bandwidth (the paper's read1/read2) and arithmetic rates (its
+    p-functions) of this GPU, measured with the library's probe kernels."""
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+    sms = tf.sm_count()
+    out = {}
+    x, y, _, _ = data[("f64", cond0)]["dot"]
+    for name, args_ in (("read1_gbs", (x, None)), ("read2_gbs", (x, y))):
+        b = x.numel() * 8 * (2 if args_[1] is not None else 1)
+        best = 1e30
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tf.probe_read(args_[0], args_[1], blocks=4 * sms, threads=512)
+            e.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(e))
+        out[name] = round(b / (best * 1e-3) / 1e9, 1)
+    blocks, threads = 4 * sms, 256
+    for kind, iters in (("fadd", 20000), ("dadd", 2000), ("dfma", 2000), ("iadd", 20000),
+                        ("fast_f32", 5000), ("rigorous_f32", 3000), ("fast_f64", 500),
+                        ("rigorous_f64", 300)):
+        tf.probe_alu(kind, iters // 10, blocks, threads, device=dev)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tf.probe_alu(kind, iters, blocks, threads, device=dev)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ops = tf.ALU_OPS_PER_ITER[tf.ALU_KINDS[kind]] * iters * blocks * threads
+        out[kind + "_gops"] = round(ops / (a.elapsed_time(e) * 1e-3) / 1e9, 1)
+    return out
+
+
+def run_e2e(args, data, ws, step_ks, dev):
+    """The step through the host-buffer C-ABI calls (pinned inputs)."""
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+    host = {}
+    for k in step_ks:
+        dt, cond, op, _, _ = k
+        if (dt, cond, op) not in host:
+            x, y, _, _ = data[(dt, cond)][op]
+            xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+            xh.copy_(x)
+            yh = None
+            if y is not None:
+                yh = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+                yh.copy_(y)
+            host[(dt, cond, op)] = (xh, yh, x, y)
+    bi = bo = 0
+    reps = max(1, min(args.steps, 3))
+
+    def one_step():
+        nonlocal bi, bo
+        for k in step_ks:
+            dt, cond, op, v, _ = k
+            xh, yh, xd, yd = host[(dt, cond, op)]
+            if op == "sum":
+                tf.sum_host(xh, v, x_dev=xd, ws=ws)
+            else:
+                tf.dot_host(xh, yh, v, x_dev=xd, y_dev=yd, ws=ws)
+
+    one_step()        # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one_step()
+    torch.cuda.synchronize()
+    dt_s = (time.perf_counter() - t0) / reps
+    n = args.n
+    step_bytes = sum(nbytes(k[0], k[2], n) for k in step_ks)
+    bo = sum(16 if k[0] == "f64" else 8 for k in step_ks)
+    return {"value": round(step_bytes / dt_s / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": bo,
+            "ms_per_step": round(dt_s * 1e3, 3), "steps": reps}
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_step(data_host, m):
+    """The oracle's sequential twofold loops (Examples 1 and 3 and their
+    TwoProduct dot forms) over the first m elements of each of the step's
+    inputs.  Returns (bytes, seconds)."""
+    import oracle as O
+    loops = {("sum", "fast"): "sumtf", ("sum", "rigorous"): "sumt",
+             ("dot", "fast"): "dottf2", ("dot", "rigorous"): "dott2"}
+    t0 = time.perf_counter()
+    b = 0
+    for (dt, cond, op), (x, y) in data_host.items():
+        for v in TWOFOLD:
+            O.loop(loops[(op, v)], x[:m], None if y is None else y[:m])
+            b += nbytes(dt, op, min(m, x.size))
+    return b, time.perf_counter() - t0
+
+
+def host_sample(data, m):
+    out = {}
+    for (dt, cond), d in data.items():
+        for op in OPS:
+            x, y, _, _ = d[op]
+            out[(dt, cond, op)] = (x[:m].cpu().numpy(), None if y is None else y[:m].cpu().numpy())
+    return out
+
+
+def run_cpu_baseline(data, m):
+    b, s = cpu_oracle_step(host_sample(data, m), m)
+    return {"value": round(b / s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d elements of each of the step's 24 inputs, the oracle's "
+                      "sequential twofold loops (one host thread, as in the paper)" % m,
+            "seconds": round(s, 2)}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return None
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    m = args.ref_sample
+    data = {}
+    for dt in ("f32", "f64"):
+        for cond in CONDS:
+            s = I.ill_conditioned(m, dt, cond, seed=0)
+            d = I.ill_conditioned(m, dt, cond, seed=1, dot=True)
+            data[(dt, cond, "sum")] = (s.x.numpy(), None)
+            data[(dt, cond, "dot")] = (d.x.numpy(), d.y.numpy())
+    for _ in range(args.warmup):
+        cpu_oracle_step(data, m)
+    tot_b = tot_s = 0.0
+    for _ in range(args.steps):
+        b, s = cpu_oracle_step(data, m)
+        tot_b += b
+        tot_s += s
+    value = tot_b / tot_s / 1e9
+    del torch
+    return {"metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_s / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded SplitMix64; ill-conditioned)", "impl": "reference",
+            "config": {"workload": "single vectors, f32+f64, twofold sum+dot, fast+rigorous, "
+                                   "cond 1e4/1e8/1e16 (24 reductions per step)",
+                       "n": m, "conds": list(CONDS)},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "N=%d per input (bounded sample of the N=2^28 workload)" % m},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--ref-sample", type=int, default=1 << 22)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probes", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="profiling: no nvidia-smi sampler")
+    ap.add_argument("--only", default="", help="profiling: comma list of kernels, e.g. f64_dot_rigorous")
+    ap.add_argument("--conds", default="1e4,1e8,1e16", help="profiling: condition numbers")
+    args = ap.parse_args(argv)
+    args.only = set(k for k in args.only.split(",") if k)
+    args.conds = tuple(float(c) for c in args.conds.split(","))
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return 0
+    import torch
+    res, data, ws, outs, ks_all, step_ks = run_gpu(args, rank, world, local)
+    if not args.no_e2e:
+        e2e = run_e2e(args, data, ws, step_ks, torch.device("cuda", local))
+        e2e["value"] = round(sum_over_ranks(e2e["value"], world), 2) if world > 1 else e2e["value"]
+        res["e2e"] = e2e
+    if rank == 0:
+        res["cpu_baseline"] = run_cpu_baseline(data, args.cpu_sample)
+        print(json.dumps(res))
+    barrier(world)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * twofold.h -- C ABI of libtwofold.so: twofold summation and dot products on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * Method (E. Latkin, "Twofold fast summation", 2013).  A twofold result is a
+ * pair (value, error) of floating-point numbers approximating an exact real
+ * as value + error (Overview; the twofold<number> type of Example 1).  The
+ * value is the floating-point sum in the library's order; the error collects
+ * the rounding errors of those additions:
+ *   TF_FAST      Dekker's FAST-TWO-SUM step per item (Theorem 1, Example 1)
+ *   TF_RIGOROUS  Knuth's TWO-SUM step per item (Theorem 2, Example 3)
+ *   TF_PLAIN     direct summation, error = 0 (Example 3, "sum")
+ *   TF_WIDE      binary32 data summed in a binary64 accumulator (the listing
+ *                after Example 3, "sumd"); binary32 data only
+ * Dot products take x[i]*y[i] in place of data[i] (end of the Algorithms
+ * section); the twofold variants also add each product's exact rounding
+ * error, from TwoProduct p = RN(x*y), ep = fma(x, y, -p), to the error term.
+ * TF_WIDE forms the product of two binary32 numbers in binary64 (exact).
+ *
+ * Reduction order.  Work is split into independent chains that follow the
+ * per-item steps above, and chain pairs are merged by TWO-SUM on the values
+ * plus one addition of the errors: (v, q) = TWO-SUM(v1, v2), e = (e1 + e2) + q.
+ * The order is a fixed function of (n, launch plan, SM count), so results are
+ * bit-reproducible run to run for a fixed plan:
+ *   single vector: with V = 16 / sizeof(element), thread g of P = grid*block
+ *   threads takes the 16-byte vectors j = g + P*m (m = 0, 1, ...) and feeds
+ *   element l of vector j to its chain (m mod U)*V + l; a trailing partial
+ *   vector is vector n/V.  Each thread folds its chains as a binary tree
+ *   (c <- c + w for w = UV/2 ... 1), each warp by an xor butterfly (offsets
+ *   16 ... 1), each block's warp pairs by the butterfly over block/32 lanes;
+ *   the last block to finish folds the block pairs (thread t takes pairs
+ *   t, t+block, ... in turn, then the same butterflies).
+ *   batched: the concatenated vector is cut into tiles of plan.tile elements;
+ *   in a segment's piece of a tile, element at tile offset r goes to lane
+ *   (r/V) mod 32, chain ((r/V)/32 mod U)*V + r mod V; lanes fold as above;
+ *   a segment spanning k tiles merges its k piece pairs by 32 lanes (lane l
+ *   takes pieces l, l+32, ...) and the butterfly.
+ * For binary32 data the cross-block (and cross-tile) merge of the twofold and
+ * wide variants runs in binary64 and the output is v = RN32(V),
+ * e = RN32((V - v) + E) from the binary64 pair (V, E); the plain variant stays
+ * in binary32 throughout.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named x, y, offsets, out, ws are DEVICE pointers owned by the
+ *     caller; the library never allocates on these paths, so the calls can be
+ *     captured in a CUDA graph.  Host pointers are named *_host.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) unless stated otherwise.
+ *   - Argument errors are detected on the host and returned before anything
+ *     is enqueued.  Launch failures return TF_ERR_CUDA.
+ *   - Element arrays need natural alignment only; 16-byte aligned arrays use
+ *     128-bit loads, others take scalar loads in the same order (same bits).
+ *   - n = 0 (or an empty segment) gives (+0, +0).  NaN/Inf inputs propagate
+ *     (value non-finite, error NaN).
+ *   - ws: workspace of at least tf_workspace_size() bytes, zero-filled before
+ *     its first use (tf_workspace_reset); every completed call leaves it
+ *     ready for the next.  Calls that share a workspace must be ordered on one
+ *     stream.
+ */
+#ifndef TWOFOLD_H
+#define TWOFOLD_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tf_stream_t;   /* same type as cudaStream_t */
+
+typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
+typedef enum { TF_PLAIN = 0, TF_FAST = 1, TF_RIGOROUS = 2, TF_WIDE = 3 } tf_variant;
+typedef enum { TF_OP_SUM = 0, TF_OP_DOT = 1 } tf_op;
+
+typedef enum {
+    TF_OK = 0,
+    TF_ERR_ARG = 1,          /* null pointer, negative size, bad enum, bad plan   */
+    TF_ERR_DTYPE = 2,        /* variant not defined for the dtype (wide + f64)    */
+    TF_ERR_WORKSPACE = 3,    /* ws smaller than tf_workspace_size()               */
+    TF_ERR_ALIGN = 4,        /* pointer not aligned to its element size           */
+    TF_ERR_CUDA = 5,         /* a CUDA runtime call failed                        */
+    TF_ERR_OFFSETS = 6,      /* device-detected: offsets not a valid CSR          */
+    TF_ERR_TIMEOUT = 7,      /* a bounded wait gave up                            */
+    TF_ERR_UNSUPPORTED = 8   /* no sm_103a device, or a size beyond the limits    */
+} tf_status;
+
+/* flags */
+#define TF_OUT_F64 0x1u      /* binary32 data: write the binary64 pair (V, E)     */
+
+/* Launch plan: the reduction order is a function of it (see above). */
+typedef struct {
+    int32_t block;           /* threads per block: 128, 256 or 512                */
+    int32_t unroll;          /* 128-bit loads per thread per step U: 1, 2 or 4;
+                                a thread runs U * (16 / sizeof(element)) chains    */
+    int32_t blocks_per_sm;   /* grid = blocks_per_sm * SM count (1..8)            */
+    int32_t tile;            /* batched only: elements per warp tile, a multiple
+                                of 32 * 16 / sizeof(element) (e.g. 4096); 0 flat  */
+} tf_plan;
+
+/* ---- single vectors ---------------------------------------------------- */
+
+/* Twofold sum of x[0..n): out receives {value, error} as two elements of the
+   data type, or two doubles when flags & TF_OUT_F64 (binary32 data).
+   Example 1 (fast), Example 3 (rigorous, direct), "sumd" listing (wide). */
+tf_status tf_sum(const void* x, int64_t n, tf_dtype dtype, tf_variant variant,
+                 void* out, void* ws, size_t ws_bytes, uint32_t flags,
+                 tf_stream_t stream);
+
+/* Twofold dot product sum x[i]*y[i], i < n (x, y of the same dtype);
+   "multiplication like a[i]*b[i] in place of data[i]" plus TwoProduct. */
+tf_status tf_dot(const void* x, const void* y, int64_t n, tf_dtype dtype,
+                 tf_variant variant, void* out, void* ws, size_t ws_bytes,
+                 uint32_t flags, tf_stream_t stream);
+
+/* ---- ragged batches (CSR) ---------------------------------------------- */
+
+/* One twofold sum per segment s < nseg of x: elements [offsets[s],
+   offsets[s+1]).  x holds n elements; offsets (device, int64, nseg + 1
+   entries) must satisfy offsets[0] = 0, offsets[s] <= offsets[s+1],
+   offsets[nseg] <= n.  out receives nseg pairs (2*nseg elements, or doubles
+   with TF_OUT_F64).  Enqueues two kernels: an offsets check and one
+   persistent reduction over all segments.  Invalid offsets are detected on
+   the device: every output pair is set to NaN and the workspace error word
+   to TF_ERR_OFFSETS (read it with tf_get_device_error). */
+tf_status tf_sum_batched(const void* x, int64_t n, const int64_t* offsets, int64_t nseg,
+                         tf_dtype dtype, tf_variant variant, void* out, void* ws,
+                         size_t ws_bytes, uint32_t flags, tf_stream_t stream);
+
+/* Per-segment twofold dot products of x and y (both n elements). */
+tf_status tf_dot_batched(const void* x, const void* y, int64_t n, const int64_t* offsets,
+                         int64_t nseg, tf_dtype dtype, tf_variant variant, void* out,
+                         void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream);
+
+/* ---- host buffers (end to end) ----------------------------------------- */
+
+/* Synchronous convenience for host data: copies x_host (n elements; pinned
+   memory for full speed) to the caller's device buffer x_dev, reduces it as
+   tf_sum does, copies the pair to out_host and waits for the stream. */
+tf_status tf_sum_host(const void* x_host, int64_t n, tf_dtype dtype, tf_variant variant,
+                      void* out_host, void* x_dev, void* ws, size_t ws_bytes,
+                      uint32_t flags, tf_stream_t stream);
+tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtype dtype,
+                      tf_variant variant, void* out_host, void* x_dev, void* y_dev,
+                      void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream);
+
+/* ---- workspace --------------------------------------------------------- */
+
+/* Bytes of workspace for a call (batched != 0: n elements, nseg segments).
+   The size covers every plan the tuner may choose for that shape. */
+tf_status tf_workspace_size(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
+                            int64_t n, int64_t nseg, size_t* bytes);
+/* Zero-fill ws (stream-ordered). */
+tf_status tf_workspace_reset(void* ws, size_t ws_bytes, tf_stream_t stream);
+/* Read and clear the device error word of ws (0 or a tf_status); waits for
+   `stream`. */
+tf_status tf_get_device_error(void* ws, size_t ws_bytes, int32_t* code, tf_stream_t stream);
+
+/* ---- plans and tuning -------------------------------------------------- */
+
+tf_status tf_plan_get(tf_op op, int batched, tf_dtype dtype, tf_variant variant, tf_plan* plan);
+tf_status tf_plan_set(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
+                      const tf_plan* plan);
+/* The launch shape a call of size n (or total elements n) would use. */
+tf_status tf_launch_shape(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
+                          int64_t n, int32_t* block, int32_t* unroll, int64_t* grid,
+                          int64_t* tile);
+/* Time every candidate plan on the given problem (device data as for the
+   calls above, y/offsets NULL where unused), `reps` timed launches each after
+   two warm-up launches, keep the fastest as the plan for its key and return
+   it.  Synchronous; not capturable. */
+tf_status tf_tune(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
+                  const void* x, const void* y, int64_t n, const int64_t* offsets,
+                  int64_t nseg, void* out, void* ws, size_t ws_bytes, int reps,
+                  tf_stream_t stream, tf_plan* best);
+/* Plans as text, one line per key: "op batched dtype variant block unroll
+   blocks_per_sm tile".  Save writes a temporary file and renames it. */
+tf_status tf_plan_save(const char* path);
+tf_status tf_plan_load(const char* path);
+
+/* ---- building blocks and probes ---------------------------------------- */
+
+/* Elementwise error-free transforms on device arrays of n elements:
+   prim 0 FAST-TWO-SUM(a, b) (Theorem 1), 1 TWO-SUM(a, b) (Theorem 2),
+   2 TwoProduct (p = RN(ab), e = fma(a, b, -p)).  Outputs to x, y. */
+tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* x, void* y,
+                  int64_t n, tf_stream_t stream);
+
+/* Memory-read probe (the paper's read1/read2): streams nbytes of x (and of y
+   when not NULL) with the reduction's 128-bit loads and no arithmetic, and
+   writes one word per block to sink (blocks words). */
+tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
+                        int32_t blocks, int32_t threads, tf_stream_t stream);
+
+/* Arithmetic probe (the paper's p-functions): each thread runs `iters`
+   iterations of 8 independent chains of one operation, from registers.
+   kind: 0 FADD, 1 DADD, 2 FFMA, 3 DFMA, 4 IADD (32-bit), 5 fast step binary32,
+   6 rigorous step binary32, 7 fast step binary64, 8 rigorous step binary64.
+   sink receives one word per thread (blocks * threads words). */
+tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
+                       tf_stream_t stream);
+
+/* ---- misc -------------------------------------------------------------- */
+const char* tf_status_string(tf_status s);
+/* SM count of the current device (0 if none). */
+int32_t tf_device_sm_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,168 @@
+// tf_aux.cu -- elementwise error-free transforms and the two measurement
+// probes (sm_103a).
+//
+//   prim_kernel   FAST-TWO-SUM / TWO-SUM / TwoProduct over arrays, the same
+//                 device functions the reductions use.
+//   read_probe    the paper's read1/read2: stream one or two arrays with the
+//                 reductions' 128-bit loads and no arithmetic.
+//   alu_probe     the paper's p-functions: the per-item operations from
+//                 registers, 8 independent chains per thread, no loads.
+#include "tf_device.cuh"
+#include "tf_internal.h"
+
+namespace tf {
+
+template <typename T>
+__global__ void prim_kernel(int prim, const T* __restrict__ a, const T* __restrict__ b,
+                            T* __restrict__ x, T* __restrict__ y, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        T u, v;
+        if (prim == 0) fast_two_sum(a[i], b[i], u, v);
+        else if (prim == 1) two_sum(a[i], b[i], u, v);
+        else two_product(a[i], b[i], u, v);
+        x[i] = u;
+        y[i] = v;
+    }
+}
+
+cudaError_t launch_prim(int prim, int dtype, const void* a, const void* b, void* x, void* y,
+                        int64_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    if (dtype == 0)
+        prim_kernel<float><<<(unsigned)blocks, 256, 0, st>>>(prim, (const float*)a, (const float*)b,
+                                                             (float*)x, (float*)y, n);
+    else
+        prim_kernel<double><<<(unsigned)blocks, 256, 0, st>>>(prim, (const double*)a, (const double*)b,
+                                                              (double*)x, (double*)y, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ read probe
+__global__ void __launch_bounds__(1024)
+read_probe(const float* __restrict__ x, const float* __restrict__ y, int64_t nvec,
+           unsigned int* __restrict__ sink) {
+    const int64_t P = (int64_t)gridDim.x * blockDim.x;
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int acc = 0;
+    for (; j + 3 * P < nvec; j += 4 * P) {
+        float r[4][4], q[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ld_stream(x + 4 * (j + u * P), r[u]);
+            if (y) ld_stream(y + 4 * (j + u * P), q[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                acc ^= __float_as_uint(r[u][l]);
+                if (y) acc ^= __float_as_uint(q[u][l]);
+            }
+    }
+    for (; j < nvec; j += P) {
+        float r[4], q[4];
+        ld_stream(x + 4 * j, r);
+        if (y) ld_stream(y + 4 * j, q);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            acc ^= __float_as_uint(r[l]);
+            if (y) acc ^= __float_as_uint(q[l]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc ^= __shfl_xor_sync(FULL, acc, o);
+    __shared__ unsigned int sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t ^= sm[w];
+        sink[blockIdx.x] = t;
+    }
+}
+
+cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
+                              int blocks, int threads, cudaStream_t st) {
+    read_probe<<<blocks, threads, 0, st>>>((const float*)x, (const float*)y, nbytes / 16,
+                                           (unsigned int*)sink);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- ALU probe
+template <int KIND>
+__global__ void __launch_bounds__(1024)
+alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int out = 0;
+    if constexpr (KIND == 0 || KIND == 2 || KIND == 5 || KIND == 6) {
+        float c[8], e[8];
+        const float d = seed * 1e-7f, m = 1.0f - seed * 1e-9f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { c[k] = seed + (float)(tid + k); e[k] = 0.0f; }
+        for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if constexpr (KIND == 0) c[k] = __fadd_rn(c[k], d);
+                else if constexpr (KIND == 2) c[k] = __fmaf_rn(c[k], m, d);
+                else if constexpr (KIND == 5) feed<FAST, false>(c[k], e[k], d, 0.0f);
+                else feed<RIGOROUS, false>(c[k], e[k], d, 0.0f);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out ^= __float_as_uint(c[k]) ^ __float_as_uint(e[k]);
+    } else if constexpr (KIND == 1 || KIND == 3 || KIND == 7 || KIND == 8) {
+        double c[8], e[8];
+        const double d = (double)seed * 1e-15, m = 1.0 - (double)seed * 1e-17;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { c[k] = (double)seed + (double)(tid + k); e[k] = 0.0; }
+        for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if constexpr (KIND == 1) c[k] = __dadd_rn(c[k], d);
+                else if constexpr (KIND == 3) c[k] = __fma_rn(c[k], m, d);
+                else if constexpr (KIND == 7) feed<FAST, false>(c[k], e[k], d, 0.0);
+                else feed<RIGOROUS, false>(c[k], e[k], d, 0.0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            unsigned long long b = __double_as_longlong(c[k]) ^ __double_as_longlong(e[k]);
+            out ^= (unsigned int)b ^ (unsigned int)(b >> 32);
+        }
+    } else {  // KIND 4: 32-bit integer adds
+        unsigned int c[8];
+        const unsigned int d = __float_as_uint(seed) | 1u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = (unsigned int)(tid + k);
+        for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) asm volatile("add.u32 %0, %0, %1;" : "+r"(c[k]) : "r"(d));
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out ^= c[k];
+    }
+    sink[tid] = out;
+}
+
+cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, int threads,
+                             cudaStream_t st) {
+    unsigned int* s = (unsigned int*)sink;
+    const float seed = 1.25f;
+    switch (kind) {
+    case 0: alu_probe<0><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 1: alu_probe<1><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 2: alu_probe<2><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 3: alu_probe<3><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 4: alu_probe<4><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 5: alu_probe<5><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 6: alu_probe<6><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 7: alu_probe<7><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 8: alu_probe<8><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tf

@@ -1,0 +1,158 @@
+// tf_flat.cu -- twofold sum / dot of one vector in one launch (sm_103a).
+//
+// Grid-stride streaming with 128-bit loads: thread g of P threads takes the
+// 16-byte vectors j = g + P*m and feeds element l of vector j to its chain
+// (m mod U)*V + l, U vectors in flight per step.  The U*V chains hide the
+// dependency of each chain's additions (the latency chain the paper breaks
+// with independent accumulators in its h-functions).  Chains fold by a
+// tree, warps by an xor butterfly, blocks through shared memory; the last
+// block to finish (a ticket in the workspace, no waiting) folds the block
+// pairs in index order and writes the result.
+#include "tf_device.cuh"
+#include "tf_internal.h"
+
+namespace tf {
+
+template <typename T, int VAR, bool DOT, int U>
+__global__ void __launch_bounds__(512)
+flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+            void* __restrict__ out, unsigned char* __restrict__ ws, int aligned, int out_f64) {
+    using A = typename Acc<T, VAR>::type;
+    using G = typename GridAcc<T, VAR>::type;
+    constexpr bool TW = twofold_v<VAR>;
+    constexpr int V = 16 / sizeof(T);
+    constexpr int C = U * V;
+
+    A s[C], e[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) { s[c] = A(0); e[c] = A(0); }
+
+    const int64_t nv = n / V;
+    const int tail = (int)(n - nv * V);
+    const int64_t P = (int64_t)gridDim.x * blockDim.x;
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+    // steps of U full vectors: vector j + u*P is step m = kU + u, chain u*V + l
+    for (; j + (U - 1) * P < nv; j += U * P) {
+        T xv[U][V], yv[U][V];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ld_vec<T, V>(x + (j + u * P) * V, aligned, xv[u]);
+            if constexpr (DOT) ld_vec<T, V>(y + (j + u * P) * V, aligned, yv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+                feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[u][l], DOT ? yv[u][l] : T(0));
+    }
+    // fewer than U full vectors left for this thread, and maybe the partial
+    // vector n/V (owned by the thread with g = (n/V) mod P)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t jj = j + u * P;
+        if (jj < nv) {
+            T xv[V], yv[V];
+            ld_vec<T, V>(x + jj * V, aligned, xv);
+            if constexpr (DOT) ld_vec<T, V>(y + jj * V, aligned, yv);
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+                feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[l], DOT ? yv[l] : T(0));
+        } else if (jj == nv && tail > 0) {
+#pragma unroll
+            for (int l = 0; l < V; ++l)
+                if (l < tail) {
+                    T a = x[jj * V + l];
+                    T b = DOT ? y[jj * V + l] : T(0);
+                    feed<VAR, DOT>(s[u * V + l], e[u * V + l], a, b);
+                }
+        }
+    }
+
+    // thread fold: tree over the chains
+#pragma unroll
+    for (int w = C / 2; w >= 1; w >>= 1)
+#pragma unroll
+        for (int c = 0; c < w; ++c) merge<TW>(s[c], e[c], s[c + w], e[c + w]);
+    A v = s[0], ev = e[0];
+
+    __shared__ A smA[64];
+    block_fold<TW>(v, ev, smA);
+
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    G* slots = reinterpret_cast<G*>(ws + kWsHeader);
+    __shared__ int am_last;
+    if (threadIdx.x == 0) {
+        slots[2 * blockIdx.x] = (G)v;
+        slots[2 * blockIdx.x + 1] = (G)ev;
+        __threadfence();
+        unsigned int t = atomicAdd(&hdr->ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+
+    // grid fold: thread t takes block pairs t, t + B, t + 2B, ... in turn
+    G gv = G(0), ge = G(0);
+    if (threadIdx.x < gridDim.x) {
+        ld_pair_cg(slots + 2 * threadIdx.x, gv, ge);
+        for (int64_t i = threadIdx.x + blockDim.x; i < gridDim.x; i += blockDim.x) {
+            G v2, e2;
+            ld_pair_cg(slots + 2 * i, v2, e2);
+            merge<TW>(gv, ge, v2, e2);
+        }
+    }
+    __shared__ G smG[64];
+    block_fold<TW>(gv, ge, smG);
+    if (threadIdx.x == 0) {
+        write_out<T, VAR, G>(out, 0, gv, ge, out_f64 != 0);
+        hdr->ticket = 0u;           // ready for the next call / graph replay
+    }
+}
+
+template <typename T, int VAR, bool DOT>
+static cudaError_t launch_u(int unroll, const void* x, const void* y, int64_t n, void* out,
+                            void* ws, int block, int64_t grid, int aligned, int out_f64,
+                            cudaStream_t st) {
+    const T* xp = static_cast<const T*>(x);
+    const T* yp = static_cast<const T*>(y);
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    switch (unroll) {
+    case 1: flat_kernel<T, VAR, DOT, 1><<<(unsigned)grid, block, 0, st>>>(xp, yp, n, out, w, aligned, out_f64); break;
+    case 2: flat_kernel<T, VAR, DOT, 2><<<(unsigned)grid, block, 0, st>>>(xp, yp, n, out, w, aligned, out_f64); break;
+    case 4: flat_kernel<T, VAR, DOT, 4><<<(unsigned)grid, block, 0, st>>>(xp, yp, n, out, w, aligned, out_f64); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int VAR>
+static cudaError_t launch_d(int dot, int unroll, const void* x, const void* y, int64_t n,
+                            void* out, void* ws, int block, int64_t grid, int aligned,
+                            int out_f64, cudaStream_t st) {
+    return dot ? launch_u<T, VAR, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st)
+               : launch_u<T, VAR, false>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+}
+
+cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void* x,
+                        const void* y, int64_t n, void* out, void* ws, int block,
+                        int64_t grid, int aligned, int out_f64, cudaStream_t st) {
+    if (dtype == 0) {
+        switch (variant) {
+        case PLAIN: return launch_d<float, PLAIN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case FAST: return launch_d<float, FAST>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case RIGOROUS: return launch_d<float, RIGOROUS>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case WIDE: return launch_d<float, WIDE>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        }
+    } else {
+        switch (variant) {
+        case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tf

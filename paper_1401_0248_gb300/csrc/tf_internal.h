@@ -1,0 +1,34 @@
+// tf_internal.h -- host-side declarations shared by the library's translation
+// units (not part of the public ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tf {
+
+// workspace header layout (device side mirrors it in tf_device.cuh)
+constexpr size_t kHeaderBytes = 256;
+constexpr int64_t kMinTile = 1024;       // smallest batched tile, in elements
+constexpr int64_t kMaxFlatGrid = 8 * 256; // blocks_per_sm <= 8, SM count <= 256
+
+// single-vector reduction: dtype 0 f32 / 1 f64, variant 0..3, dot 0/1
+cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void* x,
+                        const void* y, int64_t n, void* out, void* ws, int block,
+                        int64_t grid, int aligned, int out_f64, cudaStream_t st);
+
+// batched reduction: the offsets check, then the persistent kernel
+cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* x,
+                       const void* y, int64_t n, const int64_t* off, int64_t nseg,
+                       void* out, void* ws, size_t ws_bytes, int block, int64_t grid,
+                       int64_t tile, int aligned, int out_f64, cudaStream_t st);
+size_t csr_ws_bytes(int64_t n, int64_t nseg);
+
+cudaError_t launch_prim(int prim, int dtype, const void* a, const void* b, void* x, void* y,
+                        int64_t n, cudaStream_t st);
+cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
+                              int blocks, int threads, cudaStream_t st);
+cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, int threads,
+                             cudaStream_t st);
+
+}  // namespace tf

@@ -1,0 +1,94 @@
+"""The C-ABI library builds, loads and exports every symbol of include/twofold.h
+(CPU only: no compute calls, only host-side argument checks)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1401_0248_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "twofold.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tf_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = libbuild.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("tf_sum", "tf_dot", "tf_sum_batched", "tf_dot_batched", "tf_workspace_size",
+                 "tf_status_string", "tf_prim", "tf_tune"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1401_0248_gb300 import twofold
+    assert set(declared_functions()) == set(twofold.SIGNATURES)
+    twofold.lib()      # binds argtypes for all of them
+
+
+def test_host_side_checks_without_gpu():
+    from paper_1401_0248_gb300 import twofold
+    L = twofold.lib()
+    assert twofold.status_string(0) == "ok"
+    assert twofold.status_string(6) == "invalid CSR offsets"
+    b = C.c_size_t(0)
+    assert L.tf_workspace_size(0, 0, 0, 1, 1 << 20, 0, C.byref(b)) == 0 and b.value > 256
+    assert L.tf_workspace_size(0, 1, 0, 1, 1 << 20, 100, C.byref(b)) == 0
+    big = b.value
+    assert L.tf_workspace_size(0, 1, 0, 1, 1 << 24, 100, C.byref(b)) == 0 and b.value > big
+    # argument errors come back before any device work
+    assert L.tf_sum(None, -1, 0, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 1
+    assert L.tf_sum(None, 10, 1, 3, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 2  # wide f64
+    assert L.tf_sum(C.c_void_p(2), 10, 0, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 4
+    assert L.tf_sum(C.c_void_p(256), 10, 0, 1, C.c_void_p(256), C.c_void_p(256), 16, 0, None) == 3
+    p = twofold.Plan(100, 2, 2, 0)
+    assert L.tf_plan_set(0, 0, 0, 1, C.byref(p)) == 1          # block must be 128/256/512
+    p = twofold.Plan(256, 2, 4, 1000)
+    assert L.tf_plan_set(0, 1, 0, 1, C.byref(p)) == 1          # tile not a multiple of 128
+    assert L.tf_device_sm_count() >= 0
+
+
+def test_plan_save_load_roundtrip(tmp_path):
+    from paper_1401_0248_gb300 import twofold
+    import torch
+    before = twofold.plan_get("dot", True, torch.float64, "rigorous")
+    twofold.plan_set("dot", True, torch.float64, "rigorous", 128, 4, 8, 8192)
+    path = str(tmp_path / "plans.txt")
+    twofold.plan_save(path)
+    twofold.plan_set("dot", True, torch.float64, "rigorous", before["block"], before["unroll"],
+                     before["blocks_per_sm"], before["tile"])
+    twofold.plan_load(path)
+    assert twofold.plan_get("dot", True, torch.float64, "rigorous") == \
+        {"block": 128, "unroll": 4, "blocks_per_sm": 8, "tile": 8192}
+    twofold.plan_set("dot", True, torch.float64, "rigorous", before["block"], before["unroll"],
+                     before["blocks_per_sm"], before["tile"])
+    with open(path, "a") as f:
+        f.write("0 0 0 1 100 1 1 0\n")
+    with pytest.raises(twofold.TwofoldError):
+        twofold.plan_load(path)
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The binding raises on CPU tensors instead of computing anything."""
+    import torch
+    from paper_1401_0248_gb300 import twofold
+    with pytest.raises(ValueError):
+        twofold.sum(torch.zeros(10))
+    src = open(os.path.join(ROOT, "paper_1401_0248_gb300", "twofold.py")).read()
+    assert "oracle" not in src.replace("oracle is", "")

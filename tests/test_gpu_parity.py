@@ -1,0 +1,332 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar: the error-free transforms are bit-identical to the oracle's; every
+reduction's (value, error) is bit-identical to the oracle's sequential replay
+of the documented order for the launch shape in use; rigorous results also
+satisfy |S - (v+e)| <= u|S| + gamma_D^2 sum|x| against the exact oracle.
+Sizes span several blocks / tiles and ragged tails; edge cases: n = 0, 1,
+< one vector, misaligned pointers, empty segments, invalid offsets.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1401_0248_gb300 import inputs as I
+from paper_1401_0248_gb300 import twofold as tf
+from _helpers import U32, U64, csr_depth, flat_depth, same_bits, twofold_bound
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+TD = {"f32": torch.float32, "f64": torch.float64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(DEV)
+    assert tf.sm_count() > 0, "libtwofold.so does not see an sm_103a device"
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------ primitives
+def structured_f32(exps, nsig=40, seed=1):
+    rng = np.random.default_rng(seed)
+    sig = rng.integers(1 << 23, 1 << 24, size=nsig, dtype=np.int64)
+    sig[0], sig[1] = 1 << 23, (1 << 24) - 1
+    v = [s * np.ldexp(float(m), int(e) - 23) for e in exps for m in sig for s in (1.0, -1.0)]
+    return np.array(v, dtype=np.float32)
+
+
+def pairs(v):
+    return np.repeat(v, v.size), np.tile(v, v.size)
+
+
+F32_SETS = [range(-8, 8), range(-149, -133), range(-70, -54), range(112, 128)]
+
+
+@pytest.mark.parametrize("name", ["fast_two_sum", "two_sum", "two_product"])
+@pytest.mark.parametrize("exps", F32_SETS)
+def test_prims_f32_bit_exact_structured(name, exps):
+    a, b = pairs(structured_f32(exps))
+    with np.errstate(all="ignore"):
+        wx, wy = getattr(O, name)(a, b)
+    gx, gy = tf.prim(name, torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV))
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+
+
+def wide_f64(n, seed):
+    rng = np.random.default_rng(seed)
+    e = rng.integers(-1074, 1023, size=n)
+    m = rng.random(n) + 1.0
+    s = rng.choice([-1.0, 1.0], size=n)
+    return (s * np.ldexp(m, e)).astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["fast_two_sum", "two_sum", "two_product"])
+def test_prims_f64_bit_exact_random(name):
+    n = 1 << 20
+    a = wide_f64(n, 1)
+    b = wide_f64(n, 2)
+    b[: n // 4] = a[: n // 4] * (1 + 2.0 ** -30)            # near cancellation
+    b[n // 4: n // 2] = np.ldexp(np.random.default_rng(3).random(n // 4) + 1, -540)
+    a[n // 4: n // 2] = np.ldexp(np.random.default_rng(4).random(n // 4) + 1, -530)  # subnormal products
+    with np.errstate(all="ignore"):
+        wx, wy = getattr(O, name)(a, b)
+    gx, gy = tf.prim(name, torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV))
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+
+
+# ------------------------------------------------------------ flat path
+VARIANTS = [("sum", "plain"), ("sum", "fast"), ("sum", "rigorous"), ("dot", "plain"),
+            ("dot", "fast"), ("dot", "rigorous")]
+SIZES = [0, 1, 3, 5, 1000, 65537, (1 << 20) + 13]
+
+
+def run_flat(op, variant, x, y, out_f64=False):
+    if op == "sum":
+        return tf.sum(x, variant, out_f64=out_f64)
+    return tf.dot(x, y, variant, out_f64=out_f64)
+
+
+def check_flat(op, variant, dt, x, y, out_f64=False):
+    out = _np(run_flat(op, variant, x, y, out_f64))
+    xh, yh = _np(x), (_np(y) if y is not None else None)
+    block, unroll, grid, _ = tf.launch_shape(op, False, TD[dt], variant, xh.size)
+    want = O.replay_flat(op, variant, xh, yh, block=block, unroll=unroll, grid=grid, out_f64=out_f64)
+    assert same_bits(out, want), (op, variant, dt, xh.size, out, want)
+    return out, (block, unroll, grid)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("op,variant", VARIANTS + [("sum", "wide"), ("dot", "wide")])
+@pytest.mark.parametrize("n", SIZES)
+def test_flat_bit_exact_vs_replay(dt, op, variant, n):
+    if variant == "wide" and dt == "f64":
+        pytest.skip("wide is defined for binary32 data only")
+    x = I.normal(n, dt, seed=n % 4000, device=DEV)
+    y = I.normal(n, dt, seed=n % 4000, stream=3, device=DEV) if op == "dot" else None
+    out, (block, unroll, grid) = check_flat(op, variant, dt, x, y)
+    if dt == "f32" and variant != "plain":
+        check_flat(op, variant, dt, x, y, out_f64=True)
+    if n and variant == "rigorous":
+        ex = O.exact(_np(x), _np(y) if y is not None else None, v=float(out[0]), e=float(out[1]))
+        u = U32 if dt == "f32" else U64
+        D = flat_depth(n, 4 if dt == "f32" else 2, block, unroll, grid)
+        assert abs(ex.r) <= twofold_bound(ex.s, ex.sabs, u, 2 * D)
+
+
+@pytest.mark.parametrize("block,unroll,bps", [(128, 1, 1), (256, 4, 8), (512, 2, 4), (128, 4, 2)])
+def test_flat_every_plan_shape(block, unroll, bps):
+    n = 300007
+    for dt in ("f32", "f64"):
+        x = I.uniform(n, dt, seed=9, device=DEV)
+        y = I.uniform(n, dt, seed=9, stream=1, device=DEV)
+        for op, variant in VARIANTS:
+            before = tf.plan_get(op, False, TD[dt], variant)
+            try:
+                tf.plan_set(op, False, TD[dt], variant, block, unroll, bps)
+                check_flat(op, variant, dt, x, y if op == "dot" else None)
+            finally:
+                tf.plan_set(op, False, TD[dt], variant, before["block"], before["unroll"],
+                            before["blocks_per_sm"])
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_flat_misaligned_pointers_same_bits(dt):
+    n = 200003
+    base = I.normal(n + 3, dt, seed=4, device=DEV)
+    ybase = I.normal(n + 3, dt, seed=4, stream=1, device=DEV)
+    for off in (1, 2, 3):
+        x = base[off:off + n]               # element-aligned, not 16-byte aligned
+        y = ybase[off:off + n]
+        xc, yc = x.clone(), y.clone()      # 16-byte aligned copies
+        for variant in ("fast", "rigorous", "plain"):
+            a = _np(tf.sum(x, variant))
+            b = _np(tf.sum(xc, variant))
+            assert same_bits(a, b)
+            a = _np(tf.dot(x, yc, variant))
+            b = _np(tf.dot(xc, yc, variant))
+            assert same_bits(a, b)
+
+
+def test_flat_special_values():
+    x = torch.tensor([1.0, float("inf"), 2.0], device=DEV)
+    out = _np(tf.sum(x, "fast"))
+    assert np.isinf(out[0]) and np.isnan(out[1])
+    x = torch.tensor([1.0, float("nan")], dtype=torch.float64, device=DEV)
+    assert np.isnan(_np(tf.sum(x, "rigorous"))[0])
+    z = torch.zeros(0, device=DEV)
+    out = _np(tf.sum(z, "rigorous"))
+    assert out[0] == 0 and out[1] == 0 and not np.signbit(out[0])
+    # integers: every operation exact, so value = exact sum and error = 0
+    xi = torch.randint(-100, 100, (1 << 20,), device=DEV).float()
+    out = _np(tf.sum(xi, "rigorous"))
+    assert float(out[0]) == float(xi.long().sum().item()) and out[1] == 0
+
+
+# ------------------------------------------------------------ CSR path
+def make_csr(nseg, lmin, lmax, seed, empties=()):
+    L = I.csr_lengths(nseg, lmin, lmax, seed=seed)
+    for k in empties:
+        L[k] = 0
+    return I.csr_offsets(L)
+
+
+def check_csr(op, variant, dt, x, y, off_h, out_f64=False):
+    off = torch.from_numpy(off_h).to(DEV)
+    if op == "sum":
+        out = tf.sum_batched(x, off, variant, out_f64=out_f64)
+    else:
+        out = tf.dot_batched(x, y, off, variant, out_f64=out_f64)
+    got = _np(out)
+    xh, yh = _np(x), (_np(y) if y is not None else None)
+    _, unroll, _, tile = tf.launch_shape(op, True, TD[dt], variant, xh.size)
+    want = O.replay_csr(op, variant, xh, off_h, yh, unroll=unroll, tile=tile, out_f64=out_f64)
+    assert same_bits(got, want), (op, variant, dt)
+    return got, unroll, tile
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("op,variant", VARIANTS + [("sum", "wide"), ("dot", "wide")])
+def test_csr_bit_exact_vs_replay(dt, op, variant):
+    if variant == "wide" and dt == "f64":
+        pytest.skip("wide is defined for binary32 data only")
+    off_h = make_csr(300, 1, 20000, seed=5, empties=(0, 7, 8, 299))
+    n = int(off_h[-1]) + 5                      # x longer than the segments cover
+    x = I.normal(n, dt, seed=6, device=DEV)
+    y = I.normal(n, dt, seed=6, stream=2, device=DEV) if op == "dot" else None
+    got, unroll, tile = check_csr(op, variant, dt, x, y, off_h)
+    if dt == "f32" and variant in ("fast", "rigorous"):
+        check_csr(op, variant, dt, x, y, off_h, out_f64=True)
+    if variant == "rigorous":
+        ex = O.exact_batched(_np(x), off_h, _np(y) if y is not None else None,
+                             v=got[:, 0].astype(np.float64), e=got[:, 1].astype(np.float64))
+        u = U32 if dt == "f32" else U64
+        for s in range(300):
+            L = int(off_h[s + 1] - off_h[s])
+            D = csr_depth(max(L, 1), 4 if dt == "f32" else 2, unroll, tile)
+            assert abs(ex[s]["r"]) <= twofold_bound(ex[s]["s"], ex[s]["sabs"], u, 2 * D)
+
+
+@pytest.mark.parametrize("tile", [1024, 4096, 16384])
+def test_csr_tiles_and_long_segments(tile):
+    # one segment over many tiles, many tiny ones, and segments ending on tile edges
+    L = [tile * 40 + 17, 1, 2, 3, tile - 6, tile, 0, 2 * tile, 5, 100000, 0, 0, 31]
+    off_h = I.csr_offsets(L)
+    n = int(off_h[-1])
+    for dt in ("f32", "f64"):
+        x = I.uniform(n, dt, seed=8, device=DEV)
+        y = I.uniform(n, dt, seed=8, stream=5, device=DEV)
+        for op, variant in (("sum", "rigorous"), ("dot", "fast"), ("sum", "plain")):
+            before = tf.plan_get(op, True, TD[dt], variant)
+            try:
+                tf.plan_set(op, True, TD[dt], variant, 256, 2, 4, tile)
+                check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
+            finally:
+                tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
+                            before["blocks_per_sm"], before["tile"])
+
+
+def test_csr_invalid_offsets_flagged_then_recovers():
+    x = I.uniform(1000, "f32", seed=1, device=DEV)
+    ws = tf.workspace(tf.workspace_size("sum", True, torch.float32, "fast", 1000, 4), DEV)
+    tf.device_error(ws)                                     # clear
+    bad = torch.tensor([0, 10, 5, 20, 30], dtype=torch.int64, device=DEV)
+    out = _np(tf.sum_batched(x, bad, "fast", ws=ws))
+    assert np.all(np.isnan(out))
+    assert tf.device_error(ws) == 6                         # TF_ERR_OFFSETS
+    beyond = torch.tensor([0, 10, 2000], dtype=torch.int64, device=DEV)
+    out = _np(tf.sum_batched(x, beyond, "fast", ws=ws))
+    assert np.all(np.isnan(out)) and tf.device_error(ws) == 6
+    good = torch.tensor([0, 10, 500, 1000], dtype=torch.int64, device=DEV)
+    got = _np(tf.sum_batched(x, good, "fast", ws=ws))
+    assert tf.device_error(ws) == 0
+    _, unroll, _, tile = tf.launch_shape("sum", True, torch.float32, "fast", 1000)
+    want = O.replay_csr("sum", "fast", _np(x), _np(good), unroll=unroll, tile=tile)
+    assert same_bits(got, want)
+
+
+def test_csr_no_segments():
+    x = I.uniform(10, "f32", seed=1, device=DEV)
+    off = torch.zeros(1, dtype=torch.int64, device=DEV)
+    assert tf.sum_batched(x, off, "fast").shape == (0, 2)
+    allempty = torch.zeros(5, dtype=torch.int64, device=DEV)
+    out = _np(tf.sum_batched(x, allempty, "rigorous"))
+    assert np.all(out == 0)
+
+
+# ------------------------------------------------ reproducibility, graphs
+def test_bit_reproducible_runs_streams_and_graph():
+    n = (1 << 22) + 7
+    x = I.normal(n, "f32", seed=11, device=DEV)
+    y = I.normal(n, "f32", seed=11, stream=1, device=DEV)
+    ref = _np(tf.dot(x, y, "rigorous"))
+    for _ in range(20):
+        assert same_bits(_np(tf.dot(x, y, "rigorous")), ref)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ws2 = torch.zeros(tf.workspace_size("dot", False, torch.float32, "rigorous", n),
+                          dtype=torch.uint8, device=DEV)
+        o2 = tf.dot(x, y, "rigorous", ws=ws2)
+    s.synchronize()
+    assert same_bits(_np(o2), ref)
+    # batched under a CUDA graph, replayed
+    off_h = make_csr(2000, 16, 4096, seed=12)
+    xs = I.normal(int(off_h[-1]), "f32", seed=13, device=DEV)
+    off = torch.from_numpy(off_h).to(DEV)
+    ws = torch.zeros(tf.workspace_size("sum", True, torch.float32, "fast", xs.numel(), 2000),
+                     dtype=torch.uint8, device=DEV)
+    out = torch.empty(2000, 2, device=DEV)
+    direct = _np(tf.sum_batched(xs, off, "fast", ws=ws, out=out)).copy()
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(gs):
+        with torch.cuda.graph(g, stream=gs):
+            tf.sum_batched(xs, off, "fast", ws=ws, out=out)
+    torch.cuda.synchronize()
+    for _ in range(5):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert same_bits(_np(out), direct)
+
+
+def test_host_buffer_calls_match_device_calls():
+    n = 1 << 20
+    for dt in ("f32", "f64"):
+        x = I.normal(n, dt, seed=14).pin_memory()
+        y = I.normal(n, dt, seed=14, stream=1).pin_memory()
+        v, e = tf.sum_host(x, "rigorous")
+        d = _np(tf.sum(x.to(DEV), "rigorous"))
+        assert (v, e) == (d[0], d[1])
+        v, e = tf.dot_host(x, y, "fast")
+        d = _np(tf.dot(x.to(DEV), y.to(DEV), "fast"))
+        assert (v, e) == (d[0], d[1])
+
+
+def test_tuner_picks_a_valid_plan_and_stays_exact():
+    n = 1 << 22
+    x = I.uniform(n, "f32", seed=15, device=DEV)
+    before = tf.plan_get("sum", False, torch.float32, "rigorous")
+    try:
+        p = tf.tune("sum", "rigorous", x, reps=2)
+        assert p == tf.plan_get("sum", False, torch.float32, "rigorous")
+        check_flat("sum", "rigorous", "f32", x, None)
+    finally:
+        tf.plan_set("sum", False, torch.float32, "rigorous", before["block"], before["unroll"],
+                    before["blocks_per_sm"])
+
+
+def test_probes_run():
+    x = torch.zeros(1 << 24, device=DEV)
+    tf.probe_read(x)
+    tf.probe_read(x, x)
+    for k in tf.ALU_KINDS:
+        tf.probe_alu(k, 100, 152, 256, device=DEV)
+    torch.cuda.synchronize()
