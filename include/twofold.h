@@ -143,6 +143,26 @@ tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtyp
                       tf_variant variant, void* out_host, void* x_dev, void* y_dev,
                       void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream);
 
+/* ---- no caller workspace ----------------------------------------------- */
+
+/* tf_sum without a caller workspace, for callers that cannot allocate device
+   memory (a host framework that owns all device memory through its own pool,
+   a fixed device-memory budget that must not grow after start-up, or a
+   latency-critical path that must avoid cudaMalloc's implicit device-wide
+   synchronization).  The paper has no counterpart: this is a deployment
+   convenience.  Same kernel, launch shape and result bits as tf_sum.
+   Scratch: a library-owned device array of 33,024 bytes (a 256-byte header
+   and 2048 block pairs) on every GPU that loads the library, kept until the
+   process exits; no call allocates or frees memory.  A launch shape needing
+   more than 2048 blocks returns TF_ERR_UNSUPPORTED.  The first call on a
+   device looks up the array's device address (cudaGetSymbolAddress) with
+   that device current; make that first call before any stream capture.
+   Every call clears the array's header and shares the array, so calls that
+   overlap on the GPU (other streams, other host threads) race: order them
+   on one stream. */
+tf_status tf_sum_noalloc(const void* x, int64_t n, tf_dtype dtype, tf_variant variant,
+                         void* out, uint32_t flags, tf_stream_t stream);
+
 /* ---- workspace --------------------------------------------------------- */
 
 /* Bytes of workspace for a call (batched != 0: n elements, nseg segments).

@@ -37,6 +37,7 @@ SIGNATURES = {
     "tf_sum_batched": ([_P, _I64, _P, _I64, C.c_int, C.c_int, _P, _P, _SZ, _U32, _P], C.c_int),
     "tf_dot_batched": ([_P, _P, _I64, _P, _I64, C.c_int, C.c_int, _P, _P, _SZ, _U32, _P], C.c_int),
     "tf_sum_host": ([_P, _I64, C.c_int, C.c_int, _P, _P, _P, _SZ, _U32, _P], C.c_int),
+    "tf_sum_noalloc": ([_P, _I64, C.c_int, C.c_int, _P, _U32, _P], C.c_int),
     "tf_dot_host": ([_P, _P, _I64, C.c_int, C.c_int, _P, _P, _P, _P, _SZ, _U32, _P], C.c_int),
     "tf_workspace_size": ([C.c_int, C.c_int, C.c_int, C.c_int, _I64, _I64, C.POINTER(_SZ)], C.c_int),
     "tf_workspace_reset": ([_P, _SZ, _P], C.c_int),
