@@ -402,7 +402,8 @@ def run_probes(data, dev, stream, cond0):
     blocks, threads = 4 * sms, 256
     for kind, iters in (("fadd", 20000), ("dadd", 2000), ("dfma", 2000), ("iadd", 20000),
                         ("fast_f32", 5000), ("rigorous_f32", 3000), ("fast_f64", 500),
-                        ("rigorous_f64", 300)):
+                        ("rigorous_f64", 300), ("dadd_as_fma", 2000), ("dmul", 2000),
+                        ("cvt_f32_f64", 2000)):
         tf.probe_alu(kind, iters // 10, blocks, threads, device=dev)
         a = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
@@ -413,6 +414,61 @@ def run_probes(data, dev, stream, cond0):
         ops = tf.ALU_OPS_PER_ITER[tf.ALU_KINDS[kind]] * iters * blocks * threads
         out[kind + "_gops"] = round(ops / (a.elapsed_time(e) * 1e-3) / 1e9, 1)
     return out
+
+
+def run_batched(args, dev, stream):
+    """The ragged-batch configuration beside the step: 16,384 binary32 CSR
+    segments with log-uniform lengths in [16, 2^18] (uniform [-1, 1) data),
+    each call one offsets check plus one persistent launch, replayed from a
+    CUDA graph."""
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    from paper_1401_0248_gb300 import twofold as tf
+    nseg = 16384
+    L = I.csr_lengths(nseg, 16, 1 << 18, seed=0)
+    off_h = I.csr_offsets(L)
+    n = int(off_h[-1])
+    x = I.uniform(n, "f32", seed=1, device=dev)
+    y = I.uniform(n, "f32", seed=1, stream=1, device=dev)
+    off = torch.from_numpy(off_h).to(dev)
+    hbm, _ = load_peaks()
+    res = {"config": "16384 f32 segments, lengths log-uniform [16, 2^18], %d elements" % n,
+           "graph": True, "kernels": {}}
+    for op in OPS:
+        for v in ("plain", "fast", "rigorous"):
+            ws = torch.zeros(tf.workspace_size(op, True, torch.float32, v, n, nseg),
+                             dtype=torch.uint8, device=dev)
+            out = torch.empty(nseg, 2, device=dev)
+            if op == "sum":
+                call = (lambda v=v, ws=ws, out=out: tf.sum_batched(x, off, v, ws=ws, out=out))
+            else:
+                call = (lambda v=v, ws=ws, out=out: tf.dot_batched(x, y, off, v, ws=ws, out=out))
+            call()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            gs = torch.cuda.Stream(device=dev)
+            gs.wait_stream(stream)
+            with torch.cuda.stream(gs):
+                with torch.cuda.graph(g, stream=gs):
+                    call()
+            torch.cuda.synchronize()
+            for _ in range(args.warmup):
+                g.replay()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            reps = max(5, args.steps)
+            a.record(stream)
+            for _ in range(reps):
+                g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            byts = nbytes("f32", op, n) + 8 * (nseg + 1) + 8 * nseg
+            gbs = byts / (ms * 1e-3) / 1e9
+            res["kernels"]["f32_%s_%s" % (op, v)] = {"ms": round(ms, 4), "gbs": round(gbs, 1),
+                                                     "frac_hbm": round(gbs / hbm, 4)}
+            del g
+    return res
 
 
 def run_e2e(args, data, ws, step_ks, dev):
@@ -541,6 +597,7 @@ def main(argv=None):
     ap.add_argument("--ref-sample", type=int, default=1 << 22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probes", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="profiling: no nvidia-smi sampler")
     ap.add_argument("--only", default="", help="profiling: comma list of kernels, e.g. f64_dot_rigorous")
     ap.add_argument("--conds", default="1e4,1e8,1e16", help="profiling: condition numbers")
@@ -557,6 +614,9 @@ def main(argv=None):
         return 0
     import torch
     res, data, ws, outs, ks_all, step_ks = run_gpu(args, rank, world, local)
+    if not args.no_batched:
+        res["batched"] = run_batched(args, torch.device("cuda", local),
+                                     torch.cuda.current_stream(torch.device("cuda", local)))
     if not args.no_e2e:
         e2e = run_e2e(args, data, ws, step_ks, torch.device("cuda", local))
         e2e["value"] = round(sum_over_ranks(e2e["value"], world), 2) if world > 1 else e2e["value"]

@@ -201,7 +201,11 @@ tf_status tf_plan_load(const char* path);
 
 /* Elementwise error-free transforms on device arrays of n elements:
    prim 0 FAST-TWO-SUM(a, b) (Theorem 1), 1 TWO-SUM(a, b) (Theorem 2),
-   2 TwoProduct (p = RN(ab), e = fma(a, b, -p)).  Outputs to x, y. */
+   2 TwoProduct (p = RN(ab), e = fma(a, b, -p)); the binary64 forms the
+   reductions use, with the error (and for 4 the product) computed on the
+   integer pipe from the significands: 3 TWO-SUM, 4 TwoProduct, 5 FAST-TWO-SUM,
+   and 6 TWO-SUM entirely on the integer pipe.  3-6 give the bits of 1, 2, 0, 1
+   (binary32 data use 1, 2, 0, 1).  Outputs to x, y. */
 tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* x, void* y,
                   int64_t n, tf_stream_t stream);
 
@@ -214,7 +218,9 @@ tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink
 /* Arithmetic probe (the paper's p-functions): each thread runs `iters`
    iterations of 8 independent chains of one operation, from registers.
    kind: 0 FADD, 1 DADD, 2 FFMA, 3 DFMA, 4 IADD (32-bit), 5 fast step binary32,
-   6 rigorous step binary32, 7 fast step binary64, 8 rigorous step binary64.
+   6 rigorous step binary32, 7 fast step binary64, 8 rigorous step binary64,
+   9 binary64 add issued as fma(a, 1, b), 10 DMUL, 11 binary32 -> binary64
+   conversion (the last with a dependent integer op per iteration).
    sink receives one word per thread (blocks * threads words). */
 tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
                        tf_stream_t stream);

@@ -19,8 +19,35 @@ __global__ void prim_kernel(int prim, const T* __restrict__ a, const T* __restri
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         T u, v;
         if (prim == 0) fast_two_sum(a[i], b[i], u, v);
+        else if (prim == 5) {        // binary64 FAST-TWO-SUM with the error on the integer pipe
+            if constexpr (sizeof(T) == 8) {
+                if (!fast_two_sum_h64(a[i], b[i], u, v)) fast_two_sum(a[i], b[i], u, v);
+            } else {
+                fast_two_sum(a[i], b[i], u, v);
+            }
+        }
         else if (prim == 1) two_sum(a[i], b[i], u, v);
-        else two_product(a[i], b[i], u, v);
+        else if (prim == 2) two_product(a[i], b[i], u, v);
+        else if (prim == 3) {        // binary64 TWO-SUM with the error on the integer pipe
+            if constexpr (sizeof(T) == 8) {
+                if (!two_sum_h64(a[i], b[i], u, v)) two_sum(a[i], b[i], u, v);
+            } else {
+                two_sum(a[i], b[i], u, v);
+            }
+        } else if (prim == 6) {      // binary64 TWO-SUM entirely on the integer pipe
+            if constexpr (sizeof(T) == 8) {
+                bool sw;
+                if (!two_sum_i64(a[i], b[i], u, v, sw)) two_sum(a[i], b[i], u, v);
+            } else {
+                two_sum(a[i], b[i], u, v);
+            }
+        } else {                     // 4: binary64 TwoProduct on the integer pipe
+            if constexpr (sizeof(T) == 8) {
+                if (!two_product_i64(a[i], b[i], u, v)) two_product(a[i], b[i], u, v);
+            } else {
+                two_product(a[i], b[i], u, v);
+            }
+        }
         x[i] = u;
         y[i] = v;
     }
@@ -131,6 +158,28 @@ alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
             unsigned long long b = __double_as_longlong(c[k]) ^ __double_as_longlong(e[k]);
             out ^= (unsigned int)b ^ (unsigned int)(b >> 32);
         }
+    } else if constexpr (KIND == 9 || KIND == 10 || KIND == 11) {
+        // 9: binary64 add written as fma(a, 1, b); 10: DMUL; 11: binary32 -> binary64 convert
+        double c[8];
+        float f[8];
+        double one;
+        asm volatile("mov.b64 %0, 0x3FF0000000000000;" : "=d"(one));
+        const double d = (double)seed * 1e-15, m = 1.0 - (double)seed * 1e-17;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { c[k] = (double)seed + (double)(tid + k); f[k] = seed + k; }
+        for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if constexpr (KIND == 9) c[k] = __fma_rn(c[k], one, d);
+                else if constexpr (KIND == 10) c[k] = __dmul_rn(c[k], m);
+                else { c[k] = (double)f[k]; f[k] = __int_as_float(__float_as_int(f[k]) ^ (int)__double2hiint(c[k])); }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            unsigned long long b = __double_as_longlong(c[k]);
+            out ^= (unsigned int)b ^ (unsigned int)(b >> 32) ^ __float_as_uint(f[k]);
+        }
     } else {  // KIND 4: 32-bit integer adds
         unsigned int c[8];
         const unsigned int d = __float_as_uint(seed) | 1u;
@@ -160,6 +209,9 @@ cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, in
     case 6: alu_probe<6><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     case 7: alu_probe<7><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     case 8: alu_probe<8><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 9: alu_probe<9><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 10: alu_probe<10><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 11: alu_probe<11><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -44,11 +44,276 @@ __device__ __forceinline__ void two_sum(T a, T b, T& x, T& y) {
     y = add_rn(as, bs);
 }
 
+// TWO-SUM of two binary64 numbers on the integer pipe (GB300 issues 32-bit
+// integer operations at 64 times its binary64 rate).  x = RN(a + b) and
+// y = a + b - x are computed exactly from the integer significands:
+//   order |a| >= |b|; d = ea - eb; if d >= 55, |b| < ulp(a)/4 so x = a, y = b;
+//   else S = ma*2^d +- mb exactly (at most 108 bits), x = S rounded to 53
+//   bits to nearest even, y = the signed remainder (exact by Theorem 2).
+// Returns false, leaving x and y untouched, when an operand is zero,
+// subnormal, below 2^-969 or above 2^1021, or not finite; callers then use
+// the binary64 TWO-SUM.  Both routes give the same bits.  *swapped reports
+// |a| < |b| (the precondition of Theorem 1 fails).
+__device__ __forceinline__ bool two_sum_i64(double a, double b, double& x, double& y,
+                                            bool& swapped) {
+    unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const unsigned long long MAG = 0x7fffffffffffffffull, M52 = 0x000fffffffffffffull;
+    unsigned long long absA = A & MAG, absB = B & MAG;
+    swapped = absA < absB;
+    if (swapped) {
+        unsigned long long t = A; A = B; B = t;
+        t = absA; absA = absB; absB = t;
+    }
+    const int ea = (int)(absA >> 52), eb = (int)(absB >> 52);
+    if (eb < 54 || ea > 2044) return false;
+    const unsigned long long sa = A >> 63;
+    const int d = ea - eb;
+    if (d >= 55) {                    // |b| < ulp(a)/4: RN(a + b) = a, error b
+        x = __longlong_as_double((long long)A);
+        y = __longlong_as_double((long long)B);
+        return true;
+    }
+    const unsigned long long ma = (absA & M52) | (1ull << 52);
+    const unsigned long long mb = (absB & M52) | (1ull << 52);
+    unsigned long long lo = ma << d;
+    unsigned long long hi = d ? (ma >> (64 - d)) : 0ull;
+    if ((A ^ B) >> 63) {              // opposite signs: S = ma*2^d - mb >= 0
+        hi -= (lo < mb) ? 1ull : 0ull;
+        lo -= mb;
+    } else {
+        lo += mb;
+        hi += (lo < mb) ? 1ull : 0ull;
+    }
+    if ((hi | lo) == 0ull) {          // exact cancellation: +0, +0
+        x = 0.0;
+        y = 0.0;
+        return true;
+    }
+    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    int sh = p - 52;                  // bits below the 53-bit window
+    if (sh <= 0) {                    // S fits in 53 bits: exact sum, error +0
+        const unsigned long long q = lo << (-sh);
+        x = __longlong_as_double((long long)((sa << 63) |
+                                             ((unsigned long long)(eb + p - 52) << 52) | (q & M52)));
+        y = 0.0;
+        return true;
+    }
+    // 1 <= sh <= 56: q = S >> sh (< 2^53), rem = S mod 2^sh (from lo alone)
+    unsigned long long q = (lo >> sh) | (hi << (64 - sh));
+    const unsigned long long rem = lo & ((1ull << sh) - 1ull);
+    const unsigned long long half = 1ull << (sh - 1);
+    const bool up = rem > half || (rem == half && (q & 1ull));
+    const unsigned long long rmag = up ? ((1ull << sh) - rem) : rem;
+    q += up ? 1ull : 0ull;
+    int ex = eb + sh;                 // biased exponent of q*2^(sh + eb - 1075)
+    if (q == (1ull << 53)) { q >>= 1; ex += 1; }
+    x = __longlong_as_double((long long)((sa << 63) | ((unsigned long long)ex << 52) | (q & M52)));
+    if (rmag == 0ull) {
+        y = 0.0;
+    } else {
+        const int pr = 63 - __clzll((long long)rmag);
+        const unsigned long long mr = pr > 52 ? (rmag >> (pr - 52)) : (rmag << (52 - pr));
+        const unsigned long long sy = sa ^ (up ? 1ull : 0ull);
+        y = __longlong_as_double((long long)((sy << 63) |
+                                             ((unsigned long long)(eb + pr - 52) << 52) | (mr & M52)));
+    }
+    return true;
+}
+
+// Exact binary32 -> binary64 widening on the integer pipe (GB300's binary64
+// conversion shares the slow binary64 rate): sign, exponent + 896, significand
+// shifted by 29.  False for subnormal, infinite or NaN inputs (callers then
+// convert with the hardware); same bits either way.
+__device__ __forceinline__ bool widen_i(float a, double& r) {
+    const unsigned int u = __float_as_uint(a);
+    const unsigned int e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    if (e == 0u) {
+        if (m != 0u) return false;
+        r = __hiloint2double((int)(u & 0x80000000u), 0);
+        return true;
+    }
+    if (e == 0xffu) return false;
+    r = __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+    return true;
+}
+
+// The exact binary64 product of two binary32 numbers on the integer pipe: the
+// 48-bit product of the significands (one wide multiply) normalised into a
+// binary64 significand; the exponent stays in the normal binary64 range for
+// normal inputs.  False for subnormal, infinite or NaN inputs.
+__device__ __forceinline__ bool wide_product_i(float a, float b, double& r) {
+    const unsigned int ua = __float_as_uint(a), ub = __float_as_uint(b);
+    const unsigned int ea = (ua >> 23) & 0xffu, eb = (ub >> 23) & 0xffu;
+    const unsigned int sg = (ua ^ ub) & 0x80000000u;
+    if (((ua << 1) == 0u && eb != 0xffu) || ((ub << 1) == 0u && ea != 0xffu)) {
+        r = __hiloint2double((int)sg, 0);          // a zero times a finite number
+        return true;
+    }
+    if (ea == 0u || eb == 0u || ea == 0xffu || eb == 0xffu) return false;
+    const unsigned long long P = (unsigned long long)((ua & 0x7fffffu) | 0x800000u) *
+                                 (unsigned long long)((ub & 0x7fffffu) | 0x800000u);
+    const unsigned int top = (unsigned int)(P >> 47);          // 1: P in [2^47, 2^48)
+    const unsigned long long mant = (P << (5 + (top ^ 1u))) & 0x000fffffffffffffull;
+    const unsigned int ex = ea + eb + 769u + top;             // biased binary64 exponent
+    r = __longlong_as_double((long long)(((unsigned long long)(sg | (ex << 20)) << 32) | mant));
+    return true;
+}
+
 // TwoProduct: p = RN(ab), e = RN(ab - p) by one fused multiply-add.
 template <typename T>
 __device__ __forceinline__ void two_product(T a, T b, T& p, T& e) {
     p = mul_rn(a, b);
     e = fma_rn(a, b, -p);
+}
+
+// ---- hybrid binary64 transforms: x from one binary64 add, the error on the
+// integer pipe.  GB300's integer ALU pipe, not its binary64 pipe, limits the
+// all-integer TWO-SUM above; this split keeps both pipes busy.
+//
+// The error of x = RN(a + b) in units of 2^(emin - 1075), emin the smaller
+// exponent field: r = ma*2^(ea-emin) +- mb*2^(eb-emin) -+ mx*2^(ex-emin).
+// |a + b - x| <= min(|a|, |b|), so |r| < 2^53 and r is exact when the terms
+// are added modulo 2^64 (a shift by 64 or more leaves 0 there, as the
+// mathematical term does modulo 2^64).  If ex < emin the sum is exact.
+__device__ __forceinline__ unsigned long long shl_sat(unsigned long long v, unsigned int s) {
+    unsigned long long r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(v), "r"(s));   // s >= 64 gives 0
+    return r;
+}
+
+__device__ __forceinline__ double sum_error_h64(unsigned long long A, unsigned long long B,
+                                                int ea, int eb, int emin, double x) {
+    const unsigned long long M52 = 0x000fffffffffffffull, H = 1ull << 52;
+    const unsigned long long X = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((X >> 52) & 0x7ff);
+    if (ex < emin) return 0.0;
+    unsigned long long ta = shl_sat((A & M52) | H, (unsigned)(ea - emin));
+    unsigned long long tb = shl_sat((B & M52) | H, (unsigned)(eb - emin));
+    const unsigned long long tx = shl_sat((X & M52) | H, (unsigned)(ex - emin));
+    if ((A ^ X) >> 63) ta = 0ull - ta;          // terms signed relative to x
+    if ((B ^ X) >> 63) tb = 0ull - tb;
+    const unsigned long long r = ta + tb - tx;
+    if (r == 0ull) return 0.0;
+    const unsigned long long neg = r >> 63;
+    const unsigned long long mag = neg ? (0ull - r) : r;
+    const int pr = 63 - __clzll((long long)mag);               // <= 52
+    const unsigned long long sy = (X >> 63) ^ neg;
+    return __longlong_as_double((long long)((sy << 63) |
+                                            ((unsigned long long)(emin + pr - 52) << 52) |
+                                            ((mag << (52 - pr)) & M52)));
+}
+
+// TWO-SUM(a, b): x = RN(a + b), y = a + b - x.  False (x, y untouched) unless
+// both exponent fields lie in [54, 2044]; then the caller uses two_sum.
+__device__ __forceinline__ bool two_sum_h64(double a, double b, double& x, double& y) {
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
+    const int emin = min(ea, eb);
+    if (emin < 54 || max(ea, eb) > 2044) return false;
+    x = __dadd_rn(a, b);
+    y = sum_error_h64(A, B, ea, eb, emin, x);
+    return true;
+}
+
+// FAST-TWO-SUM(a, b) as written (x = a + b, y = b - (x - a)), for either order
+// of magnitudes.  If ea >= eb (exponent fields) it is error-free (Dekker's
+// condition) and y is the exact error.  Otherwise x - a = b - err exactly
+// (err = a + b - x), so y = b - RN(b - err); as |err| <= ulp(b), RN(b - err)
+// is b moved by 0 or one ulp(b) (0, 1 or 2 half-ulps below a power of two),
+// chosen by comparing |err| with ulp/2 (ulp/4 and 3ulp/4 below a power of
+// two), ties to even.
+__device__ __forceinline__ bool fast_two_sum_h64(double a, double b, double& x, double& y) {
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
+    const int emin = min(ea, eb);
+    if (emin < 54 || max(ea, eb) > 2044) return false;
+    x = __dadd_rn(a, b);
+    const double err = sum_error_h64(A, B, ea, eb, emin, x);
+    if (ea >= eb) { y = err; return true; }
+    const unsigned long long E = (unsigned long long)__double_as_longlong(err);
+    const unsigned long long M52 = 0x000fffffffffffffull;
+    if ((E << 1) == 0ull) { y = 0.0; return true; }
+    const int Eu = eb - 52;                               // exponent field of ulp(b)
+    const int eE = (int)((E >> 52) & 0x7ff);
+    const unsigned long long mE = E & M52, mB = B & M52;
+    const unsigned long long sb = B >> 63;
+    const bool wpos = ((E >> 63) != sb);                 // b - err moves away from zero
+    int ey;                                              // exponent field of |y| (0: y = 0)
+    unsigned long long sy = sb;
+    if (wpos || mB != 0ull) {                            // neighbours one ulp(b) apart
+        const bool move = (eE > Eu - 1) || (eE == Eu - 1 && (mE != 0ull || (mB & 1ull)));
+        ey = move ? Eu : 0;
+        if (wpos) sy ^= 1ull;
+    } else {                                             // b a power of two, moving down
+        int j;
+        if (eE < Eu - 2 || (eE == Eu - 2 && mE == 0ull)) j = 0;
+        else if (eE == Eu - 2) j = 1;
+        else if (eE == Eu - 1) j = mE < (1ull << 51) ? 1 : 2;
+        else j = 2;
+        ey = j == 0 ? 0 : (j == 1 ? Eu - 1 : Eu);
+    }
+    y = ey ? __longlong_as_double((long long)((sy << 63) | ((unsigned long long)ey << 52))) : 0.0;
+    return true;
+}
+
+// Out-of-line binary64 forms for the excluded operand ranges, kept as real
+// branches so that the common path never issues them.
+static __device__ __noinline__ double2 two_sum_slow(double a, double b) {
+    double x, y;
+    two_sum(a, b, x, y);
+    return make_double2(x, y);
+}
+static __device__ __noinline__ double2 fast_two_sum_slow(double a, double b) {
+    double x, y;
+    fast_two_sum(a, b, x, y);
+    return make_double2(x, y);
+}
+static __device__ __noinline__ double2 two_product_slow(double a, double b) {
+    double p, e;
+    two_product(a, b, p, e);
+    return make_double2(p, e);
+}
+
+// TwoProduct of two binary64 numbers on the integer pipe: the 106-bit
+// product of the significands, rounded to 53 bits to nearest even, gives p;
+// the signed remainder is e = ab - p, exact here (the cases where ab - p
+// underflows are excluded).  Returns false, leaving p and e untouched, for
+// zero, subnormal or non-finite operands and for exponent sums where p or e
+// would leave the normal range; callers then use the FMA form.  Same bits.
+__device__ __forceinline__ bool two_product_i64(double a, double b, double& p, double& e) {
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const unsigned long long M52 = 0x000fffffffffffffull;
+    const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
+    const int es = ea + eb;
+    if (ea == 0 || eb == 0 || ea == 2047 || eb == 2047 || es < 1128 || es > 3067) return false;
+    const unsigned long long ma = (A & M52) | (1ull << 52);
+    const unsigned long long mb = (B & M52) | (1ull << 52);
+    const unsigned long long lo = ma * mb;
+    const unsigned long long hi = __umul64hi(ma, mb);          // product in [2^104, 2^106)
+    const int sh = ((hi >> 41) & 1ull) ? 53 : 52;
+    unsigned long long q = (hi << (64 - sh)) | (lo >> sh);
+    const unsigned long long rem = lo & ((1ull << sh) - 1ull);
+    const unsigned long long half = 1ull << (sh - 1);
+    const bool up = rem > half || (rem == half && (q & 1ull));
+    const unsigned long long rmag = up ? ((1ull << sh) - rem) : rem;
+    q += up ? 1ull : 0ull;
+    int ex = es + sh - 1075;
+    if (q == (1ull << 53)) { q >>= 1; ex += 1; }
+    const unsigned long long sg = (A ^ B) >> 63;
+    p = __longlong_as_double((long long)((sg << 63) | ((unsigned long long)ex << 52) | (q & M52)));
+    if (rmag == 0ull) {
+        e = 0.0;
+    } else {
+        const int pr = 63 - __clzll((long long)rmag);          // <= 52
+        const unsigned long long se = sg ^ (up ? 1ull : 0ull);
+        e = __longlong_as_double((long long)((se << 63) | ((unsigned long long)(es + pr - 1127) << 52) |
+                                             ((rmag << (52 - pr)) & M52)));
+    }
+    return true;
 }
 
 // ------------------------------------------------------ accumulation types
@@ -75,11 +340,35 @@ template <int VAR> constexpr bool twofold_v = (VAR == FAST || VAR == RIGOROUS);
 template <int VAR, bool DOT, typename T, typename A>
 __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
     if constexpr (VAR == WIDE) {
-        double p = DOT ? __dmul_rn((double)a, (double)b) : (double)a;
+        double p;
+        if constexpr (DOT) {
+            if (!wide_product_i(a, b, p)) p = __dmul_rn((double)a, (double)b);
+        } else {
+            if (!widen_i(a, p)) p = (double)a;
+        }
         s = __dadd_rn(s, p);
     } else if constexpr (VAR == PLAIN) {
         T p = DOT ? mul_rn(a, b) : a;
         s = add_rn(s, p);
+    } else if constexpr (sizeof(T) == 8) {
+        // binary64: the error-free transforms take one binary64 add (or none
+        // for the product) plus integer work; the bits are those of the
+        // binary64 operation sequences of Examples 1 and 3.  The fast step is
+        // FAST-TWO-SUM(s, p) followed by e = e + y, since c = (t - s) - p = -y.
+        double p, ep = 0.0;
+        if constexpr (DOT) {
+            if (!two_product_i64(a, b, p, ep)) { const double2 r = two_product_slow(a, b); p = r.x; ep = r.y; }
+        } else {
+            p = a;
+        }
+        double t, y;
+        if constexpr (VAR == FAST) {
+            if (!fast_two_sum_h64(s, p, t, y)) { const double2 r = fast_two_sum_slow(s, p); t = r.x; y = r.y; }
+        } else {
+            if (!two_sum_h64(s, p, t, y)) { const double2 r = two_sum_slow(s, p); t = r.x; y = r.y; }
+        }
+        if constexpr (DOT) e = add_rn(e, add_rn(y, ep)); else e = add_rn(e, y);
+        s = t;
     } else {
         T p, ep = T(0);
         if constexpr (DOT) two_product(a, b, p, ep); else p = a;
@@ -108,7 +397,11 @@ __device__ __forceinline__ void merge(A& v, A& e, A v2, A e2) {
         v = add_rn(v, v2);
     } else {
         A x, q;
-        two_sum(v, v2, x, q);
+        if constexpr (sizeof(A) == 8) {
+            if (!two_sum_h64(v, v2, x, q)) { const double2 r = two_sum_slow(v, v2); x = r.x; q = r.y; }
+        } else {
+            two_sum(v, v2, x, q);
+        }
         e = add_rn(add_rn(e, e2), q);
         v = x;
     }

@@ -33,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--nseg", type=int, default=16384)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--flat-only", action="store_true")
+    ap.add_argument("--dtypes", default="f32,f64", help="comma list of f32, f64")
+    ap.add_argument("--load", default=None, help="start from this plan file")
     args = ap.parse_args(argv)
 
     dev = torch.device("cuda", 0)
@@ -40,8 +42,12 @@ def main(argv=None):
     lengths = I.csr_lengths(args.nseg, 16, 1 << 18, seed=0)
     off = torch.from_numpy(I.csr_offsets(lengths)).to(dev)
     total = int(off[-1].item())
+    if args.load:
+        tf.plan_load(args.load)
     t0 = time.time()
     for dt, td in (("f32", torch.float32), ("f64", torch.float64)):
+        if dt not in args.dtypes.split(","):
+            continue
         n = args.n
         x = I.uniform(n, dt, seed=0, device=dev)
         y = I.uniform(n, dt, seed=0, stream=1, device=dev)

@@ -81,6 +81,97 @@ def test_prims_f64_bit_exact_random(name):
     assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
 
 
+def int_two_sum_cases(n, seed):
+    """binary64 pairs that exercise every branch of the integer-pipe TWO-SUM:
+    exponent gaps 0..60, ties, cancellation, carries into a new binade,
+    near-overflow, tiny and subnormal operands, zeros and specials."""
+    rng = np.random.default_rng(seed)
+    k = n // 8
+    a = np.ldexp(rng.random(n) + 1.0, rng.integers(-60, 60, size=n))
+    gap = rng.integers(0, 61, size=n)
+    b = np.ldexp(rng.random(n) + 1.0, (np.frexp(a)[1] - 1 - gap))
+    sgn = rng.choice([-1.0, 1.0], size=(2, n))
+    a, b = a * sgn[0], b * sgn[1]
+    # ties: b = +-half an ulp of a (times an odd multiple of lower powers)
+    ulp = np.spacing(np.abs(a[:k]))
+    b[:k] = ulp * 0.5 * rng.choice([-1.0, 1.0], size=k) * (1 + 2.0 ** -rng.integers(1, 40, size=k))
+    b[k:k + k // 2] = ulp[: k // 2] * 0.5 * rng.choice([-1.0, 1.0], size=k // 2)      # exact ties
+    # cancellation and binade carries
+    b[k + k // 2: 2 * k] = -a[k + k // 2: 2 * k] * (1 + np.ldexp(1.0, -rng.integers(1, 52, size=k - k // 2)))
+    a[2 * k: 3 * k] = np.nextafter(np.ldexp(1.0, rng.integers(-20, 20, size=k)), 0)
+    b[2 * k: 3 * k] = np.spacing(a[2 * k: 3 * k]) * rng.random(k) * 2
+    # near overflow and near the lower limit of the integer path
+    a[3 * k: 3 * k + 64] = np.finfo(np.float64).max * rng.random(64)
+    b[3 * k: 3 * k + 64] = np.finfo(np.float64).max * rng.random(64)
+    a[3 * k + 64: 3 * k + 128] = np.ldexp(rng.random(64) + 1, rng.integers(-1000, -960, size=64))
+    b[3 * k + 64: 3 * k + 128] = np.ldexp(rng.random(64) + 1, rng.integers(-1074, -960, size=64))
+    a[3 * k + 128: 3 * k + 136] = [0.0, -0.0, 0.0, 1.0, np.inf, -np.inf, np.nan, 5e-324]
+    b[3 * k + 128: 3 * k + 136] = [0.0, -0.0, -0.0, -1.0, 1.0, np.inf, 1.0, -5e-324]
+    return a, b
+
+
+def test_int_two_sum_f64_bit_exact():
+    a, b = int_two_sum_cases(1 << 21, 5)
+    with np.errstate(all="ignore"):
+        wx, wy = O.two_sum(a, b)
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    gx, gy = tf.prim("two_sum_int", ta, tb)
+    hx, hy = tf.prim("two_sum", ta, tb)
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+    assert same_bits(_np(gx), _np(hx)) and same_bits(_np(gy), _np(hy))
+    gx, gy = tf.prim("two_sum_int", tb, ta)          # operand order
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+    gx, gy = tf.prim("two_sum_allint", ta, tb)        # all-integer form
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+    gx, gy = tf.prim("two_sum_allint", tb, ta)
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+
+
+def test_int_fast_two_sum_f64_bit_exact():
+    """FAST-TWO-SUM on the integer pipe: the literal algorithm's bits for any
+    order of magnitudes, including |a| < |b| where it loses error."""
+    a, b = int_two_sum_cases(1 << 21, 8)
+    rng = np.random.default_rng(10)
+    k = 1 << 18
+    a2 = np.ldexp(rng.random(k) + 1, rng.integers(-60, 2, size=k)) * rng.choice([-1.0, 1.0], size=k)
+    b2 = np.ldexp(1.0, rng.integers(0, 10, size=k)) * rng.choice([-1.0, 1.0], size=k)
+    b2[k // 2:] *= 1 + np.ldexp(1.0, -52) * rng.integers(0, 8, size=k - k // 2)
+    a = np.concatenate([a, a2, b2])
+    b = np.concatenate([b, b2, a2])
+    with np.errstate(all="ignore"):
+        wx, wy = O.fast_two_sum(a, b)
+    gx, gy = tf.prim("fast_two_sum_int", torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV))
+    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
+
+
+def int_two_product_cases(n, seed):
+    rng = np.random.default_rng(seed)
+    a = np.ldexp(rng.random(n) + 1, rng.integers(-560, 560, size=n)) * rng.choice([-1.0, 1.0], size=n)
+    b = np.ldexp(rng.random(n) + 1, rng.integers(-560, 560, size=n)) * rng.choice([-1.0, 1.0], size=n)
+    k = n // 8
+    b[:k] = np.ldexp(1.0, rng.integers(-10, 10, size=k))                        # exact products
+    a[k:2 * k] = np.ldexp(np.floor(rng.random(k) * 2 ** 26) + 2 ** 26, -26)      # short significands,
+    b[k:2 * k] = np.ldexp(np.floor(rng.random(k) * 2 ** 27) + 2 ** 27, -27)      # ties and carries
+    a[2 * k:3 * k] = np.ldexp(rng.random(k) + 1, rng.integers(-1022, -400, size=k))   # near underflow
+    b[2 * k:3 * k] = np.ldexp(rng.random(k) + 1, rng.integers(-700, -100, size=k))
+    a[3 * k:4 * k] = np.ldexp(rng.random(k) + 1, rng.integers(400, 1023, size=k))     # near overflow
+    b[3 * k:4 * k] = np.ldexp(rng.random(k) + 1, rng.integers(300, 1023, size=k))
+    a[4 * k: 4 * k + 8] = [0.0, -0.0, np.inf, np.nan, 5e-324, 1e-310, 1e308, -1e-300]
+    b[4 * k: 4 * k + 8] = [3.0, 2.0, 0.0, 1.0, 1e300, 1e10, 10.0, 1e-300]
+    return a, b
+
+
+def test_int_two_product_f64_bit_exact():
+    a, b = int_two_product_cases(1 << 21, 6)
+    with np.errstate(all="ignore"):
+        wp, we = O.two_product(a, b)
+    ta, tb = torch.from_numpy(a).to(DEV), torch.from_numpy(b).to(DEV)
+    gp, ge = tf.prim("two_product_int", ta, tb)
+    assert same_bits(_np(gp), wp) and same_bits(_np(ge), we)
+    gp, ge = tf.prim("two_product_int", tb, ta)
+    assert same_bits(_np(gp), wp) and same_bits(_np(ge), we)
+
+
 # ------------------------------------------------------------ flat path
 VARIANTS = [("sum", "plain"), ("sum", "fast"), ("sum", "rigorous"), ("dot", "plain"),
             ("dot", "fast"), ("dot", "rigorous")]
@@ -118,6 +209,37 @@ def test_flat_bit_exact_vs_replay(dt, op, variant, n):
         u = U32 if dt == "f32" else U64
         D = flat_depth(n, 4 if dt == "f32" else 2, block, unroll, grid)
         assert abs(ex.r) <= twofold_bound(ex.s, ex.sabs, u, 2 * D)
+
+
+@pytest.mark.parametrize("dt,cond", [("f64", 1e8), ("f64", 1e16), ("f64", 1e30), ("f32", 1e8)])
+def test_flat_ill_conditioned_bit_exact(dt, cond):
+    """cancelling data makes |s| < |y| common, which exercises the binary64
+    FAST-TWO-SUM's non-error-free branch and the exact-sum branches"""
+    n = (1 << 20) + 7
+    ic = I.ill_conditioned(n, dt, cond, seed=3, device=DEV)
+    icd = I.ill_conditioned(n, dt, cond, seed=4, device=DEV, dot=True)
+    for variant in ("fast", "rigorous", "plain"):
+        check_flat("sum", variant, dt, ic.x, None)
+        check_flat("dot", variant, dt, icd.x, icd.y)
+
+
+def test_flat_wide_special_values_bit_exact():
+    """zeros, subnormals and huge binary32 values take the hardware widening"""
+    rng = np.random.default_rng(12)
+    n = 200003
+    x = (rng.standard_normal(n) * 10.0 ** rng.integers(-45, 38, size=n)).astype(np.float32)
+    y = (rng.standard_normal(n) * 10.0 ** rng.integers(-45, 38, size=n)).astype(np.float32)
+    x[::7] = 0.0
+    x[1::11] = -0.0
+    y[2::13] = np.float32(1e-45)
+    x[3::17] = np.float32(3e-39)
+    with np.errstate(over="ignore"):
+        assert np.isfinite(x).all() and np.isfinite(y).all()
+    tx, ty = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
+    check_flat("sum", "wide", "f32", tx, None)
+    check_flat("dot", "wide", "f32", tx, ty)
+    check_flat("sum", "wide", "f32", tx, None, out_f64=True)
+    check_flat("dot", "wide", "f32", tx, ty, out_f64=True)
 
 
 @pytest.mark.parametrize("block,unroll,bps", [(128, 1, 1), (256, 4, 8), (512, 2, 4), (128, 4, 2)])
