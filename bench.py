@@ -52,18 +52,25 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 PLANS_PATH = os.path.join(ROOT, "paper_1401_0248_gb300", "plans_gb300.txt")
 FALLBACK_HBM_GBS = 6800.0
-FP64_INSTR_PER_CLK_PER_SM = 2.0       # 1.25 TFLOP/s FP64 (FMA = 2 flops) at 2070 MHz, 152 SMs
 
-# FP64-pipe instructions per element of each binary64 kernel (sum: add/sub
-# counts of Examples 1 and 3; dot: + multiply + fma (TwoProduct) + 1)
-FP64_OPS = {("sum", "plain"): 1, ("sum", "fast"): 4, ("sum", "rigorous"): 7,
-            ("dot", "plain"): 2, ("dot", "fast"): 7, ("dot", "rigorous"): 10}
+# Binary64-pipe instructions per element that the binary64 kernels issue:
+# the twofold steps keep two roundings on the binary64 pipe (t = s + p and
+# e = e + y; dots also q + ep) and compute the exact error terms and the
+# product on the integer pipe; plain keeps its add (and multiply).
+FP64_PIPE_OPS = {("sum", "plain"): 1, ("sum", "fast"): 2, ("sum", "rigorous"): 2,
+                 ("dot", "plain"): 2, ("dot", "fast"): 3, ("dot", "rigorous"): 3}
+# the paper's operation counts (Examples 1 and 3; dots add TwoProduct and one add)
+PAPER_OPS = {("sum", "plain"): 1, ("sum", "fast"): 4, ("sum", "rigorous"): 7,
+             ("dot", "plain"): 2, ("dot", "fast"): 7, ("dot", "rigorous"): 10}
+FALLBACK_DADD_GOPS = 528.0   # binary64 adds/s of a GB300 (1.67/clk/SM at 2.07 GHz)
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(files=("tf_device.cuh", "tf_flat.cu")):
+    """Hash of the sources a kernel is built from (the single-vector kernel by
+    default); a recorded ncu traffic figure is used only while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1401_0248_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -344,13 +351,15 @@ def run_gpu(args, rank, world, local):
         pass
     bytes_dom = nbytes(dt, op, n)
     if dt == "f64":
-        mhz = clocks.get("sm_mhz") or 2070.0
-        sms = tf.sm_count()
-        peak_ops = FP64_INSTR_PER_CLK_PER_SM * sms * mhz * 1e6 / 1e9      # G FP64 instr/s
-        ops = FP64_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
+        # bound by the binary64 pipe: its issued adds against the measured add rate
+        peak_ops = (probes or {}).get("dadd_gops") or FALLBACK_DADD_GOPS
+        ops = FP64_PIPE_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": round(ops, 1), "peak": round(peak_ops, 1),
-                    "unit": "G fp64-instr/s", "frac": round(ops / peak_ops, 4), "traffic": traffic,
-                    "kernel": dom_name, "peak_source": "2 FP64 instr/clk/SM x SMs x median SM clock",
+                    "unit": "G binary64-pipe ops/s", "frac": round(ops / peak_ops, 4),
+                    "traffic": traffic, "kernel": dom_name,
+                    "peak_source": "measured binary64 add rate (probe kind 1) on this GPU"
+                                   if probes else "fallback 528 G/s",
+                    "paper_ops_per_s_g": round(PAPER_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9, 1),
                     "hbm_gbs": round(bytes_dom / (dom_ms * 1e-3) / 1e9, 1),
                     "hbm_frac": round(bytes_dom / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
     else:
@@ -403,7 +412,8 @@ def run_probes(data, dev, stream, cond0):
     for kind, iters in (("fadd", 20000), ("dadd", 2000), ("dfma", 2000), ("iadd", 20000),
                         ("fast_f32", 5000), ("rigorous_f32", 3000), ("fast_f64", 500),
                         ("rigorous_f64", 300), ("dadd_as_fma", 2000), ("dmul", 2000),
-                        ("cvt_f32_f64", 2000)):
+                        ("cvt_f32_f64", 2000), ("dadd_as_fma_const", 2000),
+                        ("dadd_as_fma_reg", 2000)):
         tf.probe_alu(kind, iters // 10, blocks, threads, device=dev)
         a = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
@@ -471,10 +481,43 @@ def run_batched(args, dev, stream):
     return res
 
 
+def gpu_numa_cpus(dev):
+    """CPUs of the NUMA node the GPU hangs off (host buffers are placed there
+    by first touch), or None when the topology is not visible."""
+    try:
+        import torch
+        props = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/numa_node" % bus) as f:
+            node = int(f.read().strip())
+        if node < 0:
+            return None
+        with open("/sys/devices/system/node/node%d/cpulist" % node) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        return node, cpus
+    except Exception:
+        return None
+
+
 def run_e2e(args, data, ws, step_ks, dev):
     """The step through the host-buffer C-ABI calls (pinned inputs)."""
     import torch
     from paper_1401_0248_gb300 import twofold as tf
+    numa = gpu_numa_cpus(dev)
+    old_aff = None
+    if numa is not None:
+        try:
+            old_aff = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, numa[1])
+        except Exception:
+            old_aff = None
     host = {}
     for k in step_ks:
         dt, cond, op, _, _ = k
@@ -507,12 +550,15 @@ def run_e2e(args, data, ws, step_ks, dev):
         one_step()
     torch.cuda.synchronize()
     dt_s = (time.perf_counter() - t0) / reps
+    if old_aff is not None:
+        os.sched_setaffinity(0, old_aff)
     n = args.n
     step_bytes = sum(nbytes(k[0], k[2], n) for k in step_ks)
     bo = sum(16 if k[0] == "f64" else 8 for k in step_ks)
     return {"value": round(step_bytes / dt_s / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": bo,
-            "ms_per_step": round(dt_s * 1e3, 3), "steps": reps}
+            "ms_per_step": round(dt_s * 1e3, 3), "steps": reps,
+            "host_numa_node": None if numa is None else numa[0]}
 
 
 # ------------------------------------------------------------ CPU oracle

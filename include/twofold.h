@@ -12,6 +12,9 @@
  *   TF_PLAIN     direct summation, error = 0 (Example 3, "sum")
  *   TF_WIDE      binary32 data summed in a binary64 accumulator (the listing
  *                after Example 3, "sumd"); binary32 data only
+ *   TF_KAHAN     Kahan's compensated summation (Example 2): the pair is the
+ *                sum and the compensation not yet applied (-c); dots use
+ *                the rounded product, as the paper's dotk
  * Dot products take x[i]*y[i] in place of data[i] (end of the Algorithms
  * section); the twofold variants also add each product's exact rounding
  * error, from TwoProduct p = RN(x*y), ep = fma(x, y, -p), to the error term.
@@ -69,7 +72,7 @@ extern "C" {
 typedef struct CUstream_st* tf_stream_t;   /* same type as cudaStream_t */
 
 typedef enum { TF_F32 = 0, TF_F64 = 1 } tf_dtype;
-typedef enum { TF_PLAIN = 0, TF_FAST = 1, TF_RIGOROUS = 2, TF_WIDE = 3 } tf_variant;
+typedef enum { TF_PLAIN = 0, TF_FAST = 1, TF_RIGOROUS = 2, TF_WIDE = 3, TF_KAHAN = 4 } tf_variant;
 typedef enum { TF_OP_SUM = 0, TF_OP_DOT = 1 } tf_op;
 
 typedef enum {
@@ -86,6 +89,8 @@ typedef enum {
 
 /* flags */
 #define TF_OUT_F64 0x1u      /* binary32 data: write the binary64 pair (V, E)     */
+#define TF_DOT_LITERAL 0x2u  /* fast / rigorous dots: the paper's form, products
+                                rounded and their errors not tracked (dottf/dott) */
 
 /* Launch plan: the reduction order is a function of it (see above). */
 typedef struct {
@@ -197,6 +202,18 @@ tf_status tf_tune(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
 tf_status tf_plan_save(const char* path);
 tf_status tf_plan_load(const char* path);
 
+/* ---- error signalling -------------------------------------------------- */
+
+/* The paper's intended use of the error term: signal when it grows too large
+   for the working precision (the paragraph after Example 2).  Counts the
+   pairs (value, error) of `pairs` (npairs pairs of binary32 or binary64, as
+   tf_sum / tf_*_batched write them) with |error| > tau * |value|, or with a
+   non-finite member, into the device int32 *count (overwritten).  Two
+   stream-ordered operations (a 4-byte clear and one kernel); the count stays
+   on the device for later device work or an asynchronous copy. */
+tf_status tf_count_large_errors(const void* pairs, int64_t npairs, tf_dtype pair_dtype,
+                                double tau, int32_t* count, tf_stream_t stream);
+
 /* ---- building blocks and probes ---------------------------------------- */
 
 /* Elementwise error-free transforms on device arrays of n elements:
@@ -220,7 +237,9 @@ tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink
    kind: 0 FADD, 1 DADD, 2 FFMA, 3 DFMA, 4 IADD (32-bit), 5 fast step binary32,
    6 rigorous step binary32, 7 fast step binary64, 8 rigorous step binary64,
    9 binary64 add issued as fma(a, 1, b), 10 DMUL, 11 binary32 -> binary64
-   conversion (the last with a dependent integer op per iteration).
+   conversion (with a dependent integer op per iteration), 12 binary64 add
+   issued as fma(a, one, b) with `one` = 1.0 read from constant memory,
+   13 the same with `one` computed at run time in a register.
    sink receives one word per thread (blocks * threads words). */
 tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
                        tf_stream_t stream);

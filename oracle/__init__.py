@@ -23,7 +23,8 @@ from . import build as _build
 
 F32, F64 = 0, 1
 OPS = {"sum": 0, "dot": 1}
-VARIANTS = {"plain": 0, "fast": 1, "rigorous": 2, "wide": 3}
+VARIANTS = {"plain": 0, "fast": 1, "rigorous": 2, "wide": 3, "kahan": 4, "fast_literal": 5,
+            "rigorous_literal": 6}
 
 _lib = None
 

@@ -3,7 +3,9 @@
  * in the paper's order and notation.  TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
  *   sumtf  twofold fast summation ........ Example 1 (Dekker based)
- *   sumk   Kahan compensated summation ... Example 2
+ *   sumk   Kahan compensated summation ... Example 2 (returns the sum and,
+ *                                          as a second output, -c: the
+ *                                          compensation not yet applied)
  *   sumt   twofold rigorous summation .... Example 3 (Knuth based, as fixed
  *                                          in the 31-Dec-2013 revision)
  *   sum    direct summation .............. Example 3
@@ -40,7 +42,7 @@ void orc_sumk_##SUF(int64_t m, const T* data, T out[2]) {                     \
         c = (t - s) - y;                                                      \
         s = t;                                                                \
     }                                                                         \
-    out[0] = s; out[1] = 0;                                                   \
+    out[0] = s; out[1] = 0 - c;  /* the sum, and the compensation still owed */ \
 }                                                                             \
 void orc_sumtf_##SUF(int64_t m, const T* data, T out[2]) {                    \
     T s = 0, e = 0;                                                           \
@@ -107,7 +109,7 @@ void orc_dotk_##SUF(int64_t m, const T* a, const T* b, T out[2]) {            \
         c = (t - s) - y;                                                      \
         s = t;                                                                \
     }                                                                         \
-    out[0] = s; out[1] = 0;                                                   \
+    out[0] = s; out[1] = 0 - c;                                               \
 }                                                                             \
 void orc_dottf_##SUF(int64_t m, const T* a, const T* b, T out[2]) {           \
     T s = 0, e = 0;                                                           \

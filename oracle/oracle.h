@@ -100,7 +100,9 @@ double orc_exact_add_doubles(const double* t, int k);
 
 /* ---- 4. replay of the kernels' reduction order ------------------------- */
 /* op: 0 sum, 1 dot.  variant: 0 plain, 1 fast ('tf'), 2 rigorous ('t'),
-   3 wide ('d', binary32 data with binary64 accumulation).
+   3 wide ('d', binary32 data with binary64 accumulation), 4 kahan ('k',
+   Example 2), 5 fast and 6 rigorous dots with the paper's rounded product
+   (no TwoProduct term).
    out_f64 != 0 returns the binary64 grid-fold pair for binary32 data.
    out: two values of the output type (float or double). */
 int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y,

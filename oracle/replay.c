@@ -12,7 +12,9 @@
  * Knuth's TWO-SUM (Theorem 2).
  *
  * Per-item update of a chain (s, e), item y (for a dot, y = p = RN(a*b) and
- * ep = RN(a*b - p) is its exact rounding error):
+ * ep = RN(a*b - p) is its exact rounding error; the "literal" dot variants
+ * and Kahan take the rounded product alone, ep = 0, as the paper's dot
+ * functions do):
  *   plain      s <- s + y
  *   fast       t <- s + y; c <- (t - s) - y; e <- e - c; s <- t     (Ex. 1)
  *              dot: e <- e + (ep - c)
@@ -21,8 +23,14 @@
  *              dot: e <- e + ((ds + dy) + ep)
  *   wide       S <- S + y in binary64, y (or the binary64 product of two
  *              binary32 operands, which is exact) widened exactly.
- * Merge of two pairs:  (v, q) <- TWO-SUM(v1, v2);  e <- (e1 + e2) + q.
- * Plain and wide merge by one addition.  Every state starts at (+0, +0).
+ *   kahan      Example 2 with e = -c: y' <- y + e; t <- s + y';
+ *              e <- y' - (t - s); s <- t   (bit for bit Example 2's
+ *              y - c, (t - s) - y' negated, since negation is exact)
+ * Merge of two pairs:  (v, q) <- TWO-SUM(v1, v2);  e <- (e1 + e2) + q
+ * (twofold and Kahan).  Plain and wide merge by one addition.  Every state
+ * starts at (+0, +0).
+ * Variant codes: 0 plain, 1 fast, 2 rigorous, 3 wide, 4 kahan, 5 fast and
+ * 6 rigorous with the literal (rounded, error-free-less) product.
  *
  * Flat order (one vector x of n elements, launch block B, unroll U, grid G):
  *   V = 16 / sizeof(element); vector j holds elements jV .. jV+V-1.
@@ -111,7 +119,7 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
         else {
             float b = ((const float*)P->y)[i];
             if (P->variant == 3) { y = (double)a * (double)b; }           /* exact */
-            else if (P->variant == 0) { float pp = a * b; y = pp; }
+            else if (P->variant == 0 || P->variant >= 4) { float pp = a * b; y = pp; }
             else { float pp, ee; orc_two_product_f32(&a, &b, 1, &pp, &ee); y = pp; ep = ee; }
         }
     } else {
@@ -119,11 +127,12 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
         if (P->op == 0) { y = a; }
         else {
             double b = ((const double*)P->y)[i];
-            if (P->variant == 0) { y = a * b; }
+            if (P->variant == 0 || P->variant >= 4) { y = a * b; }
             else { double pp, ee; orc_two_product_f64(&a, &b, 1, &pp, &ee); y = pp; ep = ee; }
         }
     }
-    switch (P->variant) {
+    int v = P->variant == 5 ? 1 : (P->variant == 6 ? 2 : P->variant);
+    switch (v) {
     case 0:  /* plain */
         st->s = ADD(f, st->s, y);
         break;
@@ -135,6 +144,12 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
         double c = SUB(f, SUB(f, t, st->s), y);
         if (P->op == 0) st->e = SUB(f, st->e, c);
         else            st->e = ADD(f, st->e, SUB(f, ep, c));
+        st->s = t;
+        break; }
+    case 4: { /* kahan, Example 2 with e = -c */
+        double yk = ADD(f, y, st->e);
+        double t = ADD(f, st->s, yk);
+        st->e = SUB(f, yk, SUB(f, t, st->s));
         st->s = t;
         break; }
     case 2: { /* rigorous, Example 3 */
@@ -153,7 +168,7 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
 /* working precision of the in-block levels, and of the cross-block levels */
 static int f_block(const prob_t* P) { return P->dtype == ORC_F32 && P->variant != 3; }
 static int f_grid(const prob_t* P)  { return P->dtype == ORC_F32 && P->variant == 0; }
-static int twofold(const prob_t* P) { return P->variant == 1 || P->variant == 2; }
+static int twofold(const prob_t* P) { return P->variant == 1 || P->variant == 2 || P->variant >= 4; }
 
 static pr_t tree_fold(int f, int tw, pr_t* ch, int C) {
     for (int w = C / 2; w >= 1; w /= 2)
@@ -204,7 +219,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
                     void* out) {
     if (block < 32 || block > 1024 || !is_pow2(block) || !is_pow2(unroll) || unroll > 16 ||
         grid < 1 || n < 0 || (dtype != ORC_F32 && dtype != ORC_F64) || variant < 0 ||
-        variant > 3 || (variant == 3 && dtype != ORC_F32) || op < 0 || op > 1)
+        variant > 6 || (variant == 3 && dtype != ORC_F32) || op < 0 || op > 1)
         return -1;
     prob_t P = { dtype, op, variant, x, y };
     int V = (dtype == ORC_F32) ? 4 : 2;
@@ -317,7 +332,7 @@ int orc_replay_csr(int dtype, int op, int variant, const void* x, const void* y,
     int V = (dtype == ORC_F32) ? 4 : 2;
     if (!is_pow2(unroll) || unroll > 16 || tile < 32 * V || tile % (32 * V) ||
         nseg < 0 || !off || (dtype != ORC_F32 && dtype != ORC_F64) || variant < 0 ||
-        variant > 3 || (variant == 3 && dtype != ORC_F32) || op < 0 || op > 1)
+        variant > 6 || (variant == 3 && dtype != ORC_F32) || op < 0 || op > 1)
         return -1;
     for (int64_t s = 0; s < nseg; ++s) if (off[s] < 0 || off[s + 1] < off[s]) return -1;
     int64_t next = 0;

@@ -23,8 +23,10 @@ std::mutex g_mu;
 struct DevInfo { int sms = 0; int ok = -1; };
 DevInfo g_dev[64];
 
+constexpr int kVariants = 5;          // plain, fast, rigorous, wide, kahan
+
 // plans indexed [op][batched][dtype][variant]
-tf_plan g_plan[2][2][2][4];
+tf_plan g_plan[2][2][2][kVariants];
 bool g_plan_init = false;
 
 void init_plans_locked() {
@@ -32,7 +34,7 @@ void init_plans_locked() {
     for (int op = 0; op < 2; ++op)
         for (int b = 0; b < 2; ++b)
             for (int dt = 0; dt < 2; ++dt)
-                for (int v = 0; v < 4; ++v) {
+                for (int v = 0; v < kVariants; ++v) {
                     tf_plan p;
                     p.block = 512;
                     p.unroll = dt == 0 ? 2 : 2;
@@ -100,9 +102,16 @@ size_t flat_ws_bytes() { return kHeaderBytes + 16 * (size_t)tf::kMaxFlatGrid; }
 
 size_t esize(int dtype) { return dtype == 0 ? 4 : 8; }
 
+// the kernels' variant: the literal dot forms are variants 5 and 6 there
+int kernel_variant(int op, int variant, uint32_t flags) {
+    if (op == 1 && (flags & TF_DOT_LITERAL) && (variant == TF_FAST || variant == TF_RIGOROUS))
+        return variant == TF_FAST ? 5 : 6;
+    return variant;
+}
+
 tf_status common_checks(int op, int dtype, int variant, const void* x, const void* y,
                         int64_t n, void* out, void* ws, size_t ws_bytes) {
-    if (op < 0 || op > 1 || variant < 0 || variant > 3) return TF_ERR_ARG;
+    if (op < 0 || op > 1 || variant < 0 || variant >= kVariants) return TF_ERR_ARG;
     if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
     if (variant == TF_WIDE && dtype != TF_F32) return TF_ERR_DTYPE;
     if (n < 0 || !out || !ws) return TF_ERR_ARG;
@@ -127,8 +136,9 @@ tf_status run_flat(int op, const void* x, const void* y, int64_t n, int dtype, i
     const tf_plan p = force ? *force : get_plan(op, 0, dtype, variant);
     const int64_t grid = flat_grid(p, n, dtype, sms);
     const int aligned = ((uintptr_t)x % 16 == 0) && (op == 0 || (uintptr_t)y % 16 == 0);
-    cudaError_t e = tf::launch_flat(dtype, variant, op, p.unroll, x, y, n, out, ws, p.block, grid,
-                                    aligned, (flags & TF_OUT_F64) ? 1 : 0, st);
+    cudaError_t e = tf::launch_flat(dtype, kernel_variant(op, variant, flags), op, p.unroll, x, y,
+                                    n, out, ws, p.block, grid, aligned,
+                                    (flags & TF_OUT_F64) ? 1 : 0, st);
     return e == cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
 
@@ -151,9 +161,9 @@ tf_status run_csr(int op, const void* x, const void* y, int64_t n, const int64_t
     const tf_plan p = force ? *force : get_plan(op, 1, dtype, variant);
     const int64_t grid = csr_grid(p, sms);
     const int aligned = ((uintptr_t)x % 16 == 0) && (op == 0 || (uintptr_t)y % 16 == 0);
-    cudaError_t e = tf::launch_csr(dtype, variant, op, p.unroll, x, y, n, off, nseg, out, ws,
-                                   ws_bytes, p.block, grid, p.tile, aligned,
-                                   (flags & TF_OUT_F64) ? 1 : 0, st);
+    cudaError_t e = tf::launch_csr(dtype, kernel_variant(op, variant, flags), op, p.unroll, x, y,
+                                   n, off, nseg, out, ws, ws_bytes, p.block, grid, p.tile,
+                                   aligned, (flags & TF_OUT_F64) ? 1 : 0, st);
     return e == cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
 
@@ -243,7 +253,7 @@ tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtyp
 
 tf_status tf_workspace_size(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
                             int64_t n, int64_t nseg, size_t* bytes) {
-    if (!bytes || n < 0 || nseg < 0 || op < 0 || op > 1 || variant < 0 || variant > 3)
+    if (!bytes || n < 0 || nseg < 0 || op < 0 || op > 1 || variant < 0 || variant >= kVariants)
         return TF_ERR_ARG;
     if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
     *bytes = batched ? std::max(tf::csr_ws_bytes(n, nseg), flat_ws_bytes()) : flat_ws_bytes();
@@ -267,7 +277,7 @@ tf_status tf_get_device_error(void* ws, size_t ws_bytes, int32_t* code, tf_strea
 }
 
 tf_status tf_plan_get(tf_op op, int batched, tf_dtype dtype, tf_variant variant, tf_plan* plan) {
-    if (!plan || op < 0 || op > 1 || variant < 0 || variant > 3 || (dtype != 0 && dtype != 1))
+    if (!plan || op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1))
         return TF_ERR_ARG;
     *plan = get_plan(op, batched ? 1 : 0, dtype, variant);
     return TF_OK;
@@ -275,7 +285,7 @@ tf_status tf_plan_get(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
 
 tf_status tf_plan_set(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
                       const tf_plan* plan) {
-    if (!plan || op < 0 || op > 1 || variant < 0 || variant > 3 || (dtype != 0 && dtype != 1))
+    if (!plan || op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1))
         return TF_ERR_ARG;
     tf_plan p = *plan;
     if (!batched) p.tile = 0;
@@ -288,7 +298,7 @@ tf_status tf_plan_set(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
 
 tf_status tf_launch_shape(tf_op op, int batched, tf_dtype dtype, tf_variant variant, int64_t n,
                           int32_t* block, int32_t* unroll, int64_t* grid, int64_t* tile) {
-    if (op < 0 || op > 1 || variant < 0 || variant > 3 || (dtype != 0 && dtype != 1) || n < 0)
+    if (op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1) || n < 0)
         return TF_ERR_ARG;
     int sms = 0;
     tf_status s = check_device(&sms);
@@ -364,7 +374,7 @@ tf_status tf_plan_save(const char* path) {
         for (int op = 0; op < 2; ++op)
             for (int b = 0; b < 2; ++b)
                 for (int dt = 0; dt < 2; ++dt)
-                    for (int v = 0; v < 4; ++v) {
+                    for (int v = 0; v < kVariants; ++v) {
                         const tf_plan& p = g_plan[op][b][dt][v];
                         fprintf(f, "%d %d %d %d %d %d %d %d\n", op, b, dt, v, p.block, p.unroll,
                                 p.blocks_per_sm, p.tile);
@@ -387,12 +397,12 @@ tf_status tf_plan_load(const char* path) {
         int op, b, dt, v; tf_plan p;
         if (sscanf(line, "%d %d %d %d %d %d %d %d", &op, &b, &dt, &v, &p.block, &p.unroll,
                    &p.blocks_per_sm, &p.tile) != 8 ||
-            op < 0 || op > 1 || b < 0 || b > 1 || dt < 0 || dt > 1 || v < 0 || v > 3 ||
+            op < 0 || op > 1 || b < 0 || b > 1 || dt < 0 || dt > 1 || v < 0 || v >= kVariants ||
             !plan_valid(p, b, dt)) {
             rs = TF_ERR_ARG;
             break;
         }
-        rows.push_back({((op * 2 + b) * 2 + dt) * 4 + v, p});
+        rows.push_back({((op * 2 + b) * 2 + dt) * kVariants + v, p});
     }
     fclose(f);
     if (rs != TF_OK) return rs;
@@ -400,9 +410,22 @@ tf_status tf_plan_load(const char* path) {
     init_plans_locked();
     for (auto& r : rows) {
         const int k = r.first;
-        g_plan[k / 16][(k / 8) % 2][(k / 4) % 2][k % 4] = r.second;
+        g_plan[k / (4 * kVariants)][(k / (2 * kVariants)) % 2][(k / kVariants) % 2]
+              [k % kVariants] = r.second;
     }
     return TF_OK;
+}
+
+tf_status tf_count_large_errors(const void* pairs, int64_t npairs, tf_dtype pair_dtype,
+                                double tau, int32_t* count, tf_stream_t stream) {
+    if (npairs < 0 || !count || (npairs > 0 && !pairs) || !(tau >= 0.0)) return TF_ERR_ARG;
+    if (pair_dtype != TF_F32 && pair_dtype != TF_F64) return TF_ERR_DTYPE;
+    if ((uintptr_t)pairs % esize(pair_dtype) || (uintptr_t)count % 4) return TF_ERR_ALIGN;
+    int sms = 0;
+    tf_status s = check_device(&sms);
+    if (s != TF_OK) return s;
+    return tf::launch_large_errors(pairs, npairs, pair_dtype, tau, count, (cudaStream_t)stream) ==
+                   cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
 
 tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* x, void* y,
@@ -430,7 +453,7 @@ tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink
 
 tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
                        tf_stream_t stream) {
-    if (kind < 0 || kind > 11 || iters < 0 || !sink || blocks < 1 || threads < 32 ||
+    if (kind < 0 || kind > 13 || iters < 0 || !sink || blocks < 1 || threads < 32 ||
         threads > 1024 || threads % 32)
         return TF_ERR_ARG;
     int sms = 0;

@@ -66,6 +66,33 @@ cudaError_t launch_prim(int prim, int dtype, const void* a, const void* b, void*
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- error signalling
+template <typename T>
+__global__ void large_error_kernel(const T* __restrict__ pairs, int64_t npairs, double tau,
+                                   int* __restrict__ count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const double v = (double)pairs[2 * i], e = (double)pairs[2 * i + 1];
+        // NaN compares false, so non-finite pairs count as flagged
+        local += (fabs(e) <= tau * fabs(v) && isfinite(v) && isfinite(e)) ? 0 : 1;
+    }
+    local = __reduce_add_sync(FULL, local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+cudaError_t launch_large_errors(const void* pairs, int64_t npairs, int dtype, double tau,
+                                int* count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), st);
+    if (e != cudaSuccess || npairs == 0) return e;
+    const int64_t blocks = std::min<int64_t>((npairs + 255) / 256, 152 * 8);
+    if (dtype == 0)
+        large_error_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float*)pairs, npairs, tau, count);
+    else
+        large_error_kernel<double><<<(unsigned)blocks, 256, 0, st>>>((const double*)pairs, npairs, tau, count);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ read probe
 __global__ void __launch_bounds__(1024)
 read_probe(const float* __restrict__ x, const float* __restrict__ y, int64_t nvec,
@@ -118,6 +145,8 @@ cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void
 }
 
 // ------------------------------------------------------------- ALU probe
+__constant__ double kProbeOne = 1.0;     // opaque to the compiler: a runtime 1.0
+
 template <int KIND>
 __global__ void __launch_bounds__(1024)
 alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
@@ -156,6 +185,23 @@ alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             unsigned long long b = __double_as_longlong(c[k]) ^ __double_as_longlong(e[k]);
+            out ^= (unsigned int)b ^ (unsigned int)(b >> 32);
+        }
+    } else if constexpr (KIND == 12 || KIND == 13) {
+        // binary64 add issued as fma(a, one, b) with `one` = 1.0 read from constant
+        // memory (12) or computed from a runtime value in a register (13)
+        double c[8];
+        const double one = KIND == 12 ? kProbeOne : (double)(seed > 0.0f) + (double)(iters < 0);
+        const double d = (double)seed * 1e-15;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[k] = (double)seed + (double)(tid + k);
+        for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c[k] = __fma_rn(c[k], one, d);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            unsigned long long b = __double_as_longlong(c[k]);
             out ^= (unsigned int)b ^ (unsigned int)(b >> 32);
         }
     } else if constexpr (KIND == 9 || KIND == 10 || KIND == 11) {
@@ -212,6 +258,8 @@ cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, in
     case 9: alu_probe<9><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     case 10: alu_probe<10><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     case 11: alu_probe<11><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 12: alu_probe<12><<<blocks, threads, 0, st>>>(iters, s, seed); break;
+    case 13: alu_probe<13><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -6,9 +6,9 @@
 // grid takes a contiguous run of tiles.  Inside a tile the warp reduces each
 // segment's piece: lane l takes the 16-byte vector slots l, l+32, ... of the
 // tile, slot m-th for the lane feeding chains (m mod U)*V + (element mod V).
-// Elements outside the piece are fed as +0, which leaves a chain's bits
-// unchanged, so the chain assignment is the documented one with no branches
-// in the streaming loop.  A segment inside one tile is written directly; a
+// Elements outside the piece are fed as +0, which leaves a twofold, plain or
+// wide chain's bits unchanged (Kahan chains skip them), so the chain
+// assignment is the documented one with no branches in the streaming loop.  A segment inside one tile is written directly; a
 // segment over k tiles leaves k piece pairs in the workspace and the warp that
 // completes the k-th piece (a per-segment ticket, no waiting) merges them in
 // tile order.  A first small kernel checks the offsets, clears the tickets
@@ -107,29 +107,48 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
                         const int64_t mhi = qb >= lane ? (qb - lane) / 32 : -1;
                         for (int64_t mb = (mlo / U) * U; mb <= mhi; mb += U) {
                             T xv[U][V], yv[U][V];
+                            // Kahan chains skip the slots outside the piece (a +0 item
+                            // would apply their pending compensation); every other
+                            // variant takes them as +0, which leaves its bits unchanged
+                            unsigned int live = ~0u;
+                            // slot addresses grow with m, so the step's U vectors all lie
+                            // inside the piece iff its first and last ones do
+                            const int64_t b0 = tlo + (lane + 32 * mb) * V;
+                            const int64_t b1 = b0 + (int64_t)(32 * V) * (U - 1);
+                            if (mb >= mlo && mb + (U - 1) <= mhi && b0 >= pa && b1 + V <= pb) {
 #pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const int64_t m = mb + u;
-                                const int64_t base = tlo + (lane + 32 * m) * V;
-                                if (m >= mlo && m <= mhi && base >= pa && base + V <= pb) {
-                                    ld_vec<T, V>(x + base, aligned, xv[u]);
-                                    if constexpr (DOT) ld_vec<T, V>(y + base, aligned, yv[u]);
-                                } else {
+                                for (int u = 0; u < U; ++u) {
+                                    ld_vec<T, V>(x + b0 + (int64_t)(32 * V) * u, aligned, xv[u]);
+                                    if constexpr (DOT) ld_vec<T, V>(y + b0 + (int64_t)(32 * V) * u, aligned, yv[u]);
+                                }
+                            } else {
 #pragma unroll
-                                    for (int l = 0; l < V; ++l) {
-                                        const int64_t i = base + l;
-                                        const bool in = m >= mlo && m <= mhi && i >= pa && i < pb;
-                                        xv[u][l] = in ? x[i] : T(0);
-                                        if constexpr (DOT) yv[u][l] = in ? y[i] : T(0);
+                                for (int u = 0; u < U; ++u) {
+                                    const int64_t m = mb + u;
+                                    const int64_t base = b0 + (int64_t)(32 * V) * u;
+                                    if (m >= mlo && m <= mhi && base >= pa && base + V <= pb) {
+                                        ld_vec<T, V>(x + base, aligned, xv[u]);
+                                        if constexpr (DOT) ld_vec<T, V>(y + base, aligned, yv[u]);
+                                    } else {
+#pragma unroll
+                                        for (int l = 0; l < V; ++l) {
+                                            const int64_t i = base + l;
+                                            const bool in = m >= mlo && m <= mhi && i >= pa && i < pb;
+                                            xv[u][l] = in ? x[i] : T(0);
+                                            if constexpr (DOT) yv[u][l] = in ? y[i] : T(0);
+                                            if (!in) live &= ~(1u << (u * V + l));
+                                        }
                                     }
                                 }
                             }
 #pragma unroll
                             for (int u = 0; u < U; ++u)
 #pragma unroll
-                                for (int l = 0; l < V; ++l)
+                                for (int l = 0; l < V; ++l) {
+                                    if (step_v<VAR> == KAHAN && !((live >> (u * V + l)) & 1u)) continue;
                                     feed<VAR, DOT>(cs[u * V + l], ce[u * V + l], xv[u][l],
                                                    DOT ? yv[u][l] : T(0));
+                                }
                         }
 #pragma unroll
                         for (int w = C / 2; w >= 1; w >>= 1)
@@ -241,12 +260,18 @@ cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* 
         case FAST: return launch_d<float, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case RIGOROUS: return launch_d<float, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case WIDE: return launch_d<float, WIDE>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
+        case KAHAN: return launch_d<float, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
+        case FAST_LIT: return dot ? launch_u<float, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
+        case RIG_LIT: return dot ? launch_u<float, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
         }
     } else {
         switch (variant) {
         case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
+        case KAHAN: return launch_d<double, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
+        case FAST_LIT: return dot ? launch_u<double, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
+        case RIG_LIT: return dot ? launch_u<double, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
         }
     }
     return cudaErrorInvalidValue;

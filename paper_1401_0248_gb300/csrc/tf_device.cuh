@@ -10,7 +10,10 @@
 
 namespace tf {
 
-enum Variant : int { PLAIN = 0, FAST = 1, RIGOROUS = 2, WIDE = 3 };
+// KAHAN is Example 2; FAST_LIT and RIG_LIT are the fast and rigorous dots with
+// the paper's rounded product alone (no TwoProduct term).
+enum Variant : int { PLAIN = 0, FAST = 1, RIGOROUS = 2, WIDE = 3, KAHAN = 4, FAST_LIT = 5,
+                     RIG_LIT = 6 };
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -261,6 +264,10 @@ __device__ __forceinline__ bool fast_two_sum_h64(double a, double b, double& x, 
 
 // Out-of-line binary64 forms for the excluded operand ranges, kept as real
 // branches so that the common path never issues them.
+static __device__ __noinline__ double widen_slow(float a) { return (double)a; }
+static __device__ __noinline__ double wide_product_slow(float a, float b) {
+    return __dmul_rn((double)a, (double)b);
+}
 static __device__ __noinline__ double2 two_sum_slow(double a, double b) {
     double x, y;
     two_sum(a, b, x, y);
@@ -325,7 +332,9 @@ template <> struct Acc<float, WIDE> { using type = double; };
 template <typename T, int VAR> struct GridAcc { using type = double; };
 template <> struct GridAcc<float, PLAIN> { using type = float; };
 
-template <int VAR> constexpr bool twofold_v = (VAR == FAST || VAR == RIGOROUS);
+template <int VAR> constexpr bool twofold_v = (VAR != PLAIN && VAR != WIDE);
+// the per-item step after the product: literal dots step like the sums
+template <int VAR> constexpr int step_v = VAR == FAST_LIT ? FAST : (VAR == RIG_LIT ? RIGOROUS : VAR);
 
 // One item into one chain (s, e).  Sums: y = x.  Dots: y = RN(x*y) and, for
 // the twofold variants, ep = its TwoProduct error.
@@ -339,12 +348,14 @@ template <int VAR> constexpr bool twofold_v = (VAR == FAST || VAR == RIGOROUS);
 //                         in binary64)
 template <int VAR, bool DOT, typename T, typename A>
 __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
+    constexpr int STEP = step_v<VAR>;
+    constexpr bool TPROD = DOT && (VAR == FAST || VAR == RIGOROUS);   // TwoProduct error kept
     if constexpr (VAR == WIDE) {
         double p;
         if constexpr (DOT) {
-            if (!wide_product_i(a, b, p)) p = __dmul_rn((double)a, (double)b);
+            if (!wide_product_i(a, b, p)) p = wide_product_slow(a, b);
         } else {
-            if (!widen_i(a, p)) p = (double)a;
+            if (!widen_i(a, p)) p = widen_slow(a);
         }
         s = __dadd_rn(s, p);
     } else if constexpr (VAR == PLAIN) {
@@ -353,29 +364,45 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
     } else if constexpr (sizeof(T) == 8) {
         // binary64: the error-free transforms take one binary64 add (or none
         // for the product) plus integer work; the bits are those of the
-        // binary64 operation sequences of Examples 1 and 3.  The fast step is
-        // FAST-TWO-SUM(s, p) followed by e = e + y, since c = (t - s) - p = -y.
+        // binary64 operation sequences of Examples 1-3.  The fast step is
+        // FAST-TWO-SUM(s, p) followed by e = e + y, since c = (t - s) - p = -y;
+        // Kahan's step is FAST-TWO-SUM(s, p + e): e <- (p + e) - (t - s).
         double p, ep = 0.0;
-        if constexpr (DOT) {
+        if constexpr (TPROD) {
             if (!two_product_i64(a, b, p, ep)) { const double2 r = two_product_slow(a, b); p = r.x; ep = r.y; }
+        } else if constexpr (DOT) {
+            double unused;
+            if (!two_product_i64(a, b, p, unused)) p = two_product_slow(a, b).x;
         } else {
             p = a;
         }
         double t, y;
-        if constexpr (VAR == FAST) {
-            if (!fast_two_sum_h64(s, p, t, y)) { const double2 r = fast_two_sum_slow(s, p); t = r.x; y = r.y; }
+        if constexpr (STEP == KAHAN) {
+            const double yk = add_rn(p, e);
+            if (!fast_two_sum_h64(s, yk, t, y)) { const double2 r = fast_two_sum_slow(s, yk); t = r.x; y = r.y; }
+            e = y;
         } else {
-            if (!two_sum_h64(s, p, t, y)) { const double2 r = two_sum_slow(s, p); t = r.x; y = r.y; }
+            if constexpr (STEP == FAST) {
+                if (!fast_two_sum_h64(s, p, t, y)) { const double2 r = fast_two_sum_slow(s, p); t = r.x; y = r.y; }
+            } else {
+                if (!two_sum_h64(s, p, t, y)) { const double2 r = two_sum_slow(s, p); t = r.x; y = r.y; }
+            }
+            if constexpr (TPROD) e = add_rn(e, add_rn(y, ep)); else e = add_rn(e, y);
         }
-        if constexpr (DOT) e = add_rn(e, add_rn(y, ep)); else e = add_rn(e, y);
         s = t;
     } else {
         T p, ep = T(0);
-        if constexpr (DOT) two_product(a, b, p, ep); else p = a;
-        if constexpr (VAR == FAST) {
+        if constexpr (TPROD) two_product(a, b, p, ep); else p = DOT ? mul_rn(a, b) : a;
+        if constexpr (STEP == KAHAN) {
+            // Example 2 with e = -c: y' = y - c = y + e, c = (t - s) - y' = -e
+            const T yk = add_rn(p, e);
+            const T t = add_rn(s, yk);
+            e = sub_rn(yk, sub_rn(t, s));
+            s = t;
+        } else if constexpr (STEP == FAST) {
             T t = add_rn(s, p);
             T c = sub_rn(sub_rn(t, s), p);
-            if constexpr (DOT) e = add_rn(e, sub_rn(ep, c)); else e = sub_rn(e, c);
+            if constexpr (TPROD) e = add_rn(e, sub_rn(ep, c)); else e = sub_rn(e, c);
             s = t;
         } else {
             T t = add_rn(s, p);
@@ -383,7 +410,7 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
             T dy = sub_rn(p, yt);
             T ds = sub_rn(s, sub_rn(t, yt));
             T q = add_rn(ds, dy);
-            if constexpr (DOT) e = add_rn(e, add_rn(q, ep)); else e = add_rn(e, q);
+            if constexpr (TPROD) e = add_rn(e, add_rn(q, ep)); else e = add_rn(e, q);
             s = t;
         }
     }

@@ -144,12 +144,18 @@ cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void*
         case FAST: return launch_d<float, FAST>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case RIGOROUS: return launch_d<float, RIGOROUS>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case WIDE: return launch_d<float, WIDE>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case KAHAN: return launch_d<float, KAHAN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case FAST_LIT: return dot ? launch_u<float, FAST_LIT, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st) : cudaErrorInvalidValue;
+        case RIG_LIT: return dot ? launch_u<float, RIG_LIT, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st) : cudaErrorInvalidValue;
         }
     } else {
         switch (variant) {
         case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case KAHAN: return launch_d<double, KAHAN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case FAST_LIT: return dot ? launch_u<double, FAST_LIT, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st) : cudaErrorInvalidValue;
+        case RIG_LIT: return dot ? launch_u<double, RIG_LIT, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st) : cudaErrorInvalidValue;
         }
     }
     return cudaErrorInvalidValue;

@@ -26,6 +26,8 @@ size_t csr_ws_bytes(int64_t n, int64_t nseg);
 
 cudaError_t launch_prim(int prim, int dtype, const void* a, const void* b, void* x, void* y,
                         int64_t n, cudaStream_t st);
+cudaError_t launch_large_errors(const void* pairs, int64_t npairs, int dtype, double tau,
+                                int* count, cudaStream_t st);
 cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
                               int blocks, int threads, cudaStream_t st);
 cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, int threads,

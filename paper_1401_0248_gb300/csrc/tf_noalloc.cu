@@ -55,7 +55,7 @@ tf_status noalloc_scratch(void** addr) {
 extern "C" tf_status tf_sum_noalloc(const void* x, int64_t n, tf_dtype dtype,
                                     tf_variant variant, void* out, uint32_t flags,
                                     tf_stream_t stream) {
-    if (variant < TF_PLAIN || variant > TF_WIDE) return TF_ERR_ARG;
+    if (variant < TF_PLAIN || variant > TF_KAHAN) return TF_ERR_ARG;
     if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
     if (variant == TF_WIDE && dtype != TF_F32) return TF_ERR_DTYPE;
     if (n < 0 || !out || (n > 0 && !x)) return TF_ERR_ARG;

@@ -52,7 +52,7 @@ def main(argv=None):
         x = I.uniform(n, dt, seed=0, device=dev)
         y = I.uniform(n, dt, seed=0, stream=1, device=dev)
         for op in ("sum", "dot"):
-            for variant in ("plain", "fast", "rigorous", "wide"):
+            for variant in ("plain", "fast", "rigorous", "wide", "kahan"):
                 if variant == "wide" and dt == "f64":
                     continue
                 p = tf.tune(op, variant, x, y if op == "dot" else None, reps=args.reps)
@@ -63,7 +63,7 @@ def main(argv=None):
         xs = I.uniform(total, dt, seed=1, device=dev)
         ys = I.uniform(total, dt, seed=1, stream=1, device=dev)
         for op in ("sum", "dot"):
-            for variant in ("plain", "fast", "rigorous", "wide"):
+            for variant in ("plain", "fast", "rigorous", "wide", "kahan"):
                 if variant == "wide" and dt == "f64":
                     continue
                 p = tf.tune(op, variant, xs, ys if op == "dot" else None, offsets=off,

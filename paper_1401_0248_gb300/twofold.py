@@ -22,9 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtwofold.so")
 
 DTYPES = {torch.float32: 0, torch.float64: 1}
-VARIANTS = {"plain": 0, "fast": 1, "rigorous": 2, "wide": 3}
+VARIANTS = {"plain": 0, "fast": 1, "rigorous": 2, "wide": 3, "kahan": 4}
 OPS = {"sum": 0, "dot": 1}
 OUT_F64 = 0x1
+DOT_LITERAL = 0x2
 STATUS = {0: "TF_OK", 1: "TF_ERR_ARG", 2: "TF_ERR_DTYPE", 3: "TF_ERR_WORKSPACE",
           4: "TF_ERR_ALIGN", 5: "TF_ERR_CUDA", 6: "TF_ERR_OFFSETS", 7: "TF_ERR_TIMEOUT",
           8: "TF_ERR_UNSUPPORTED"}
@@ -51,6 +52,7 @@ SIGNATURES = {
     "tf_plan_save": ([C.c_char_p], C.c_int),
     "tf_plan_load": ([C.c_char_p], C.c_int),
     "tf_prim": ([C.c_int, C.c_int, _P, _P, _P, _P, _I64, _P], C.c_int),
+    "tf_count_large_errors": ([_P, _I64, C.c_int, C.c_double, _P, _P], C.c_int),
     "tf_probe_read": ([_P, _P, _I64, _P, _I32, _I32, _P], C.c_int),
     "tf_probe_alu": ([C.c_int, _I64, _P, _I32, _I32, _P], C.c_int),
     "tf_status_string": ([C.c_int], C.c_char_p),
@@ -168,16 +170,19 @@ def sum(x, variant="fast", *, out_f64=False, out=None, ws=None):  # noqa: A001 -
     return out
 
 
-def dot(x, y, variant="fast", *, out_f64=False, out=None, ws=None):
-    """Twofold dot product of two 1-D CUDA tensors: tensor([value, error])."""
+def dot(x, y, variant="fast", *, out_f64=False, out=None, ws=None, literal=False):
+    """Twofold dot product of two 1-D CUDA tensors: tensor([value, error]).
+    literal=True: the paper's dot form (products rounded, their errors not
+    tracked) for the fast and rigorous variants."""
     x, y = _flat(x), _flat(y)
     if x.dtype != y.dtype or x.numel() != y.numel() or x.device != y.device:
         raise ValueError("twofold.dot: x and y must match in dtype, length and device")
     out = _out(x, None, out_f64, out)
     if ws is None:
         ws = workspace(workspace_size("dot", False, x.dtype, variant, x.numel()), x.device)
+    flags = (OUT_F64 if out_f64 else 0) | (DOT_LITERAL if literal else 0)
     rc = lib().tf_dot(_ptr(x), _ptr(y), x.numel(), _dt(x), VARIANTS[variant], _ptr(out), _ptr(ws),
-                      ws.numel(), OUT_F64 if out_f64 else 0, _stream(x))
+                      ws.numel(), flags, _stream(x))
     _check("tf_dot", rc)
     return out
 
@@ -205,7 +210,7 @@ def sum_batched(x, offsets, variant="fast", *, out_f64=False, out=None, ws=None)
     return out
 
 
-def dot_batched(x, y, offsets, variant="fast", *, out_f64=False, out=None, ws=None):
+def dot_batched(x, y, offsets, variant="fast", *, out_f64=False, out=None, ws=None, literal=False):
     """One twofold dot product per CSR segment: (nseg, 2)."""
     x, y = _flat(x), _flat(y)
     if x.dtype != y.dtype or x.numel() != y.numel():
@@ -215,11 +220,25 @@ def dot_batched(x, y, offsets, variant="fast", *, out_f64=False, out=None, ws=No
     out = _out(x, nseg, out_f64, out)
     if ws is None:
         ws = workspace(workspace_size("dot", True, x.dtype, variant, x.numel(), nseg), x.device)
+    flags = (OUT_F64 if out_f64 else 0) | (DOT_LITERAL if literal else 0)
     rc = lib().tf_dot_batched(_ptr(x), _ptr(y), x.numel(), _ptr(offsets), nseg, _dt(x),
-                              VARIANTS[variant], _ptr(out), _ptr(ws), ws.numel(),
-                              OUT_F64 if out_f64 else 0, _stream(x))
+                              VARIANTS[variant], _ptr(out), _ptr(ws), ws.numel(), flags,
+                              _stream(x))
     _check("tf_dot_batched", rc)
     return out
+
+
+def count_large_errors(pairs, tau, count=None):
+    """Number of pairs (value, error) with |error| > tau * |value| (or not
+    finite), as a device int32 tensor; pairs is an (n, 2) or (2,) tensor."""
+    if not pairs.is_cuda or not pairs.is_contiguous() or pairs.dtype not in DTYPES:
+        raise ValueError("count_large_errors: a contiguous CUDA float32/float64 tensor of pairs")
+    if count is None:
+        count = torch.empty(1, dtype=torch.int32, device=pairs.device)
+    _check("tf_count_large_errors", lib().tf_count_large_errors(_ptr(pairs), pairs.numel() // 2,
+                                                                _dt(pairs), float(tau), _ptr(count),
+                                                                _stream(pairs)))
+    return count
 
 
 def device_error(ws=None, device=None):
@@ -345,8 +364,9 @@ def probe_read(x, y=None, blocks=None, threads=512, sink=None):
 
 ALU_KINDS = {"fadd": 0, "dadd": 1, "ffma": 2, "dfma": 3, "iadd": 4, "fast_f32": 5,
              "rigorous_f32": 6, "fast_f64": 7, "rigorous_f64": 8, "dadd_as_fma": 9,
-             "dmul": 10, "cvt_f32_f64": 11}
-ALU_OPS_PER_ITER = {0: 8, 1: 8, 2: 8, 3: 8, 4: 8, 5: 32, 6: 56, 7: 32, 8: 56, 9: 8, 10: 8, 11: 8}
+             "dmul": 10, "cvt_f32_f64": 11, "dadd_as_fma_const": 12, "dadd_as_fma_reg": 13}
+ALU_OPS_PER_ITER = {0: 8, 1: 8, 2: 8, 3: 8, 4: 8, 5: 32, 6: 56, 7: 32, 8: 56, 9: 8, 10: 8, 11: 8,
+                    12: 8, 13: 8}
 
 
 def probe_alu(kind, iters, blocks, threads, sink=None, device=None):

@@ -242,6 +242,84 @@ def test_flat_wide_special_values_bit_exact():
     check_flat("dot", "wide", "f32", tx, ty, out_f64=True)
 
 
+# the paper's Kahan summation (Example 2) and its literal dot forms
+EXTRA = [("sum", "kahan", False), ("dot", "kahan", False), ("dot", "fast", True),
+         ("dot", "rigorous", True)]
+
+
+def oracle_variant(variant, literal):
+    return variant + "_literal" if literal else variant
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("op,variant,literal", EXTRA)
+@pytest.mark.parametrize("n", [1, 7, 65537, (1 << 20) + 3])
+def test_flat_kahan_and_literal_dots_bit_exact(dt, op, variant, literal, n):
+    x = I.normal(n, dt, seed=n % 4000 + 7, device=DEV)
+    y = I.normal(n, dt, seed=n % 4000 + 7, stream=3, device=DEV)
+    for out_f64 in ((False, True) if dt == "f32" else (False,)):
+        if op == "sum":
+            got = _np(tf.sum(x, variant, out_f64=out_f64))
+        else:
+            got = _np(tf.dot(x, y, variant, out_f64=out_f64, literal=literal))
+        block, unroll, grid, _ = tf.launch_shape(op, False, TD[dt], variant, n)
+        want = O.replay_flat(op, oracle_variant(variant, literal), _np(x),
+                             _np(y) if op == "dot" else None, block=block, unroll=unroll,
+                             grid=grid, out_f64=out_f64)
+        assert same_bits(got, want), (dt, op, variant, literal, n)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_csr_kahan_and_literal_dots_bit_exact(dt):
+    off_h = make_csr(200, 1, 30000, seed=15, empties=(3, 4))
+    n = int(off_h[-1])
+    x = I.normal(n, dt, seed=16, device=DEV)
+    y = I.normal(n, dt, seed=16, stream=2, device=DEV)
+    off = torch.from_numpy(off_h).to(DEV)
+    for op, variant, literal in EXTRA:
+        if op == "sum":
+            got = _np(tf.sum_batched(x, off, variant))
+        else:
+            got = _np(tf.dot_batched(x, y, off, variant, literal=literal))
+        _, unroll, _, tile = tf.launch_shape(op, True, TD[dt], variant, n)
+        want = O.replay_csr(op, oracle_variant(variant, literal), _np(x), off_h,
+                            _np(y) if op == "dot" else None, unroll=unroll, tile=tile)
+        assert same_bits(got, want), (dt, op, variant, literal)
+
+
+def test_kahan_accuracy_between_direct_and_twofold():
+    """the paper's accuracy table ordering on uniform data: direct worst,
+    Kahan and twofold fast far better (binary32, 1M elements)"""
+    x = I.uniform(1 << 20, "f32", seed=17, lo=0.0, device=DEV)
+    ex = O.exact(_np(x))
+    d = _np(tf.sum(x, "plain", out_f64=True))
+    k = _np(tf.sum(x, "kahan", out_f64=True))
+    t = _np(tf.sum(x, "fast", out_f64=True))
+    err = lambda v, e=0.0: abs(float(O.exact_add(ex.s, ex.s_lo, -v, -e))) / ex.s
+    assert err(k[0], k[1]) < err(d[0]) and err(t[0], t[1]) < err(d[0])
+
+
+def test_count_large_errors():
+    rng = np.random.default_rng(18)
+    for dt in (np.float32, np.float64):
+        pairs = np.stack([rng.standard_normal(100000), rng.standard_normal(100000) * 1e-6], 1).astype(dt)
+        pairs[::97, 1] = pairs[::97, 0] * 0.5           # large relative errors
+        pairs[5, 0] = np.nan
+        pairs[6, 1] = np.inf
+        tau = 1e-3
+        want = int(np.sum(~((np.abs(pairs[:, 1].astype(np.float64)) <= tau * np.abs(pairs[:, 0].astype(np.float64)))
+                            & np.isfinite(pairs[:, 0]) & np.isfinite(pairs[:, 1]))))
+        got = tf.count_large_errors(torch.from_numpy(pairs).to(DEV), tau)
+        assert int(got.item()) == want
+    # chained after a batched reduction, on the device
+    off_h = make_csr(50, 1, 1000, seed=19)
+    x = I.normal(int(off_h[-1]), "f32", seed=19, device=DEV)
+    out = tf.sum_batched(x, torch.from_numpy(off_h).to(DEV), "rigorous")
+    cnt = tf.count_large_errors(out, 0.0)
+    o = _np(out)
+    assert int(cnt.item()) == int(np.sum(o[:, 1] != 0))
+
+
 @pytest.mark.parametrize("block,unroll,bps", [(128, 1, 1), (256, 4, 8), (512, 2, 4), (128, 4, 2)])
 def test_flat_every_plan_shape(block, unroll, bps):
     n = 300007

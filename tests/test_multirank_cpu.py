@@ -1,0 +1,87 @@
+"""Multi-rank logic on CPU (no GPU): the benchmark's aggregation over ranks
+with a world_size-2 gloo process group, and the shard-and-merge reading of
+the method (each rank reduces its own contiguous shard to a pair; the pairs
+merge by TWO-SUM in fixed rank order), emulated with the oracle.
+
+The path shards into independent problems, so bench.py --gpus N runs one
+problem per rank with no collective on the data path; the only cross-rank
+operations are the timing barrier, the max of the step time and the sum of
+the bytes, exercised here.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import oracle as O
+from paper_1401_0248_gb300 import inputs as I
+from _helpers import U64, twofold_bound
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank), TF_BENCH_BACKEND="gloo")
+    import bench
+    r, w, _ = bench.dist_setup()
+    assert (r, w) == (rank, world)
+    step_ms = [12.5, 17.25][rank]
+    mx = bench.max_over_ranks(step_ms, w)
+    tot = bench.sum_over_ranks(1000.0 * (rank + 1), w)
+    bench.barrier(w)
+    q.put((rank, mx, tot))
+    dist.destroy_process_group()
+
+
+def test_bench_aggregation_over_two_gloo_ranks():
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, mx, tot in got:
+        assert mx == 17.25          # the slowest rank's step time
+        assert tot == 3000.0        # bytes of all ranks
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    import bench
+    args = type("A", (), {"ref_sample": 1024, "steps": 1, "warmup": 3})()
+    assert bench.run_reference(args, rank=1, world=2) is None
+
+
+@pytest.mark.parametrize("shards", [2, 3, 8])
+def test_shard_and_merge_emulation(shards):
+    """Each shard's pair comes from the paper's rigorous loop (Example 3); the
+    shard pairs merge in rank order with TWO-SUM plus one add of the errors.
+    The result obeys the twofold bound with depth n/shards + shards + 1."""
+    n = 1 << 18
+    ic = I.ill_conditioned(n, "f64", 1e12, seed=31)
+    x = ic.x.numpy()
+    cuts = [n * g // shards for g in range(shards + 1)]
+    pairs = [O.loop("sumt", x[cuts[g]:cuts[g + 1]]) for g in range(shards)]
+    v, e = pairs[0]
+    for v2, e2 in pairs[1:]:
+        xs, ys = O.two_sum(np.array([v]), np.array([v2]))
+        e = (e + e2) + ys[0]
+        v = xs[0]
+    r = O.exact(x, v=float(v), e=float(e))
+    D = n // shards + shards + 1
+    assert abs(r.r) <= twofold_bound(r.s, r.sabs, U64, D)
+    # a different sharding changes the bits of the value but not the bound
+    assert abs(r.rv) > abs(r.r)

@@ -19,7 +19,10 @@ from paper_1401_0248_gb300 import inputs as I
 
 LOOP = {("sum", "plain"): "sum", ("sum", "fast"): "sumtf", ("sum", "rigorous"): "sumt",
         ("sum", "wide"): "sumd", ("dot", "plain"): "dot", ("dot", "fast"): "dottf2",
-        ("dot", "rigorous"): "dott2", ("dot", "wide"): "dotd"}
+        ("dot", "rigorous"): "dott2", ("dot", "wide"): "dotd", ("sum", "kahan"): "sumk",
+        ("dot", "kahan"): "dotk", ("dot", "fast_literal"): "dottf",
+        ("dot", "rigorous_literal"): "dott"}
+TWOFOLD = ("fast", "rigorous", "kahan", "fast_literal", "rigorous_literal")
 
 
 class Arith:
@@ -80,7 +83,7 @@ def compose_flat(op, variant, x, y, block, unroll, grid, out_f64=False):
     n = x.size
     nv, tail = n // V, n % V
     P = grid * block
-    tw = variant in ("fast", "rigorous")
+    tw = variant in TWOFOLD
     ab = Arith(f32 and variant != "wide", tw)
     ag = Arith(f32 and variant == "plain", tw)
     C = unroll * V
@@ -127,6 +130,10 @@ CASES = [
     ("dot", "wide", np.float32, 1203, 32, 4, 1),
     ("sum", "fast", np.float64, 3001, 32, 4, 5),
     ("sum", "rigorous", np.float64, 2500, 64, 2, 2),
+    ("sum", "kahan", np.float32, 2049, 64, 2, 3),
+    ("dot", "kahan", np.float64, 1777, 32, 1, 2),
+    ("dot", "fast_literal", np.float32, 1500, 32, 2, 2),
+    ("dot", "rigorous_literal", np.float64, 1501, 64, 1, 3),
 ]
 
 
@@ -188,7 +195,7 @@ def compose_csr(op, variant, x, y, off, unroll, tile, out_f64=False):
     dt = x.dtype.type
     f32 = dt == np.float32
     V = 4 if f32 else 2
-    tw = variant in ("fast", "rigorous")
+    tw = variant in TWOFOLD
     ab = Arith(f32 and variant != "wide", tw)
     ag = Arith(f32 and variant == "plain", tw)
     C = unroll * V
@@ -229,6 +236,7 @@ def compose_csr(op, variant, x, y, off, unroll, tile, out_f64=False):
     ("sum", "fast", np.float32, 1, 128), ("sum", "rigorous", np.float64, 2, 128),
     ("dot", "fast", np.float64, 1, 64), ("dot", "rigorous", np.float32, 2, 256),
     ("sum", "plain", np.float32, 1, 128), ("dot", "wide", np.float32, 1, 128),
+    ("sum", "kahan", np.float64, 2, 128), ("dot", "rigorous_literal", np.float32, 1, 128),
 ])
 def test_replay_csr_matches_composition(op, variant, dt, unroll, tile):
     s = "f32" if dt == np.float32 else "f64"
