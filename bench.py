@@ -6,9 +6,9 @@ N = 2^28 elements, binary32 and binary64, twofold sum and dot with the fast
 condition numbers 1e4, 1e8 and 1e16 (half the entries with exponents spread
 over 0..E, the rest cancelling them, seeded synthetic data).  One step is one
 pass of all 24 twofold reductions (2 dtypes x 2 ops x 2 variants x 3
-condition numbers).  Plain binary32/binary64 sums and dots and the binary64
-accumulator ('wide', binary32 data) run alongside on the same data and are
-reported per kernel, not in the step.
+condition numbers).  Plain binary32/binary64 sums and dots and the wider
+accumulators ('wide': binary32 data in binary64, binary64 data in binary128)
+run alongside on the same data and are reported per kernel, not in the step.
 
 value    whole-step algorithmic bytes / device time (CUDA events, inputs
          resident in HBM, every input larger than L2).
@@ -216,8 +216,7 @@ def kernel_list(include_baselines, conds=CONDS, only=None):
                     ks.append((dt, cond, op, v, True))
                 if include_baselines:
                     ks.append((dt, cond, op, "plain", False))
-                    if dt == "f32":
-                        ks.append((dt, cond, op, "wide", False))
+                    ks.append((dt, cond, op, "wide", False))
     if only:
         ks = [k for k in ks if "%s_%s_%s" % (k[0], k[2], k[3]) in only]
         ks = [(a, b, c, d, True) for a, b, c, d, _ in ks]

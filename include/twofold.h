@@ -10,15 +10,18 @@
  *   TF_FAST      Dekker's FAST-TWO-SUM step per item (Theorem 1, Example 1)
  *   TF_RIGOROUS  Knuth's TWO-SUM step per item (Theorem 2, Example 3)
  *   TF_PLAIN     direct summation, error = 0 (Example 3, "sum")
- *   TF_WIDE      binary32 data summed in a binary64 accumulator (the listing
- *                after Example 3, "sumd"); binary32 data only
+ *   TF_WIDE      a wider accumulator, error = 0 or the accumulator's tail:
+ *                binary32 data in binary64 (the listing after Example 3,
+ *                "sumd"); binary64 data in IEEE binary128 computed with
+ *                integer arithmetic (the paper's __float128 comparison),
+ *                output (RN64(S), RN64(S - RN64(S)))
  *   TF_KAHAN     Kahan's compensated summation (Example 2): the pair is the
  *                sum and the compensation not yet applied (-c); dots use
  *                the rounded product, as the paper's dotk
  * Dot products take x[i]*y[i] in place of data[i] (end of the Algorithms
  * section); the twofold variants also add each product's exact rounding
  * error, from TwoProduct p = RN(x*y), ep = fma(x, y, -p), to the error term.
- * TF_WIDE forms the product of two binary32 numbers in binary64 (exact).
+ * TF_WIDE forms the product exactly in its accumulator format.
  *
  * Reduction order.  Work is split into independent chains that follow the
  * per-item steps above, and chain pairs are merged by TWO-SUM on the values
@@ -78,7 +81,7 @@ typedef enum { TF_OP_SUM = 0, TF_OP_DOT = 1 } tf_op;
 typedef enum {
     TF_OK = 0,
     TF_ERR_ARG = 1,          /* null pointer, negative size, bad enum, bad plan   */
-    TF_ERR_DTYPE = 2,        /* variant not defined for the dtype (wide + f64)    */
+    TF_ERR_DTYPE = 2,        /* not a supported element type                      */
     TF_ERR_WORKSPACE = 3,    /* ws smaller than tf_workspace_size()               */
     TF_ERR_ALIGN = 4,        /* pointer not aligned to its element size           */
     TF_ERR_CUDA = 5,         /* a CUDA runtime call failed                        */

@@ -22,7 +22,12 @@
  *              e <- e + (ds + dy); s <- t                            (Ex. 3)
  *              dot: e <- e + ((ds + dy) + ep)
  *   wide       S <- S + y in binary64, y (or the binary64 product of two
- *              binary32 operands, which is exact) widened exactly.
+ *              binary32 operands, which is exact) widened exactly; for
+ *              binary64 data the accumulator is binary128 (the paper's
+ *              __float128 'sumd'), y or the binary128 product of two
+ *              binary64 operands (exact) added with one binary128 rounding,
+ *              chains merged by binary128 additions, output
+ *              (RN64(S), RN64(S - RN64(S))).
  *   kahan      Example 2 with e = -c: y' <- y + e; t <- s + y';
  *              e <- y' - (t - s); s <- t   (bit for bit Example 2's
  *              y - c, (t - s) - y' negated, since negation is exact)
@@ -81,7 +86,8 @@ static inline double SUB(int f32, double a, double b) {
     return a - b;
 }
 
-typedef struct { double s, e; } pr_t;
+/* chain state: (s, e) in the working precision, or a binary128 accumulator q */
+typedef struct { double s, e; _Float128 q; } pr_t;
 
 static inline void two_sum(int f, double a, double b, double* x, double* y) {
     double xx = ADD(f, a, b);
@@ -93,9 +99,11 @@ static inline void two_sum(int f, double a, double b, double* x, double* y) {
     *y = ADD(f, as, bs);
 }
 
-/* merge in working precision f; twofold = 0 for plain/wide (one add) */
+/* merge in working precision f (2: binary128); twofold = 0 for plain/wide (one add) */
 static inline pr_t merge(int f, int twofold, pr_t a, pr_t b) {
     pr_t r;
+    r.q = 0;
+    if (f == 2) { r.s = 0.0; r.e = 0.0; r.q = a.q + b.q; return r; }
     if (!twofold) { r.s = ADD(f, a.s, b.s); r.e = 0.0; return r; }
     double v, q;
     two_sum(f, a.s, b.s, &v, &q);
@@ -132,6 +140,12 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
         }
     }
     int v = P->variant == 5 ? 1 : (P->variant == 6 ? 2 : P->variant);
+    if (P->dtype == ORC_F64 && P->variant == 3) {          /* binary128 accumulator */
+        const double a = ((const double*)P->x)[i];
+        if (P->op == 0) st->q = st->q + (_Float128)a;
+        else st->q = st->q + (_Float128)a * (_Float128)((const double*)P->y)[i];
+        return;
+    }
     switch (v) {
     case 0:  /* plain */
         st->s = ADD(f, st->s, y);
@@ -165,9 +179,16 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
     }
 }
 
-/* working precision of the in-block levels, and of the cross-block levels */
-static int f_block(const prob_t* P) { return P->dtype == ORC_F32 && P->variant != 3; }
-static int f_grid(const prob_t* P)  { return P->dtype == ORC_F32 && P->variant == 0; }
+/* working precision of the in-block levels, and of the cross-block levels:
+   0 binary64, 1 binary32, 2 binary128 */
+static int f_block(const prob_t* P) {
+    if (P->dtype == ORC_F64 && P->variant == 3) return 2;
+    return P->dtype == ORC_F32 && P->variant != 3;
+}
+static int f_grid(const prob_t* P)  {
+    if (P->dtype == ORC_F64 && P->variant == 3) return 2;
+    return P->dtype == ORC_F32 && P->variant == 0;
+}
 static int twofold(const prob_t* P) { return P->variant == 1 || P->variant == 2 || P->variant >= 4; }
 
 static pr_t tree_fold(int f, int tw, pr_t* ch, int C) {
@@ -190,7 +211,7 @@ static pr_t butterfly(int f, int tw, pr_t* v, int W) {
 static pr_t lane_fold(int f, int tw, const pr_t* p, int64_t k, int lanes) {
     pr_t v[32];
     for (int l = 0; l < lanes; ++l) {
-        pr_t a = { 0.0, 0.0 };
+        pr_t a = { 0.0, 0.0, 0 };
         if (l < k) {
             a = p[l];
             for (int64_t i = l + lanes; i < k; i += lanes) a = merge(f, tw, a, p[i]);
@@ -201,6 +222,12 @@ static pr_t lane_fold(int f, int tw, const pr_t* p, int64_t k, int lanes) {
 }
 
 static void write_out(const prob_t* P, pr_t r, int out_f64, void* out) {
+    if (P->dtype == ORC_F64 && P->variant == 3) {
+        double* o = (double*)out;
+        o[0] = (double)r.q;
+        o[1] = (double)(r.q - (_Float128)o[0]);
+        return;
+    }
     if (P->dtype == ORC_F64) {
         double* o = (double*)out; o[0] = r.s; o[1] = r.e; return;
     }
@@ -219,7 +246,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
                     void* out) {
     if (block < 32 || block > 1024 || !is_pow2(block) || !is_pow2(unroll) || unroll > 16 ||
         grid < 1 || n < 0 || (dtype != ORC_F32 && dtype != ORC_F64) || variant < 0 ||
-        variant > 6 || (variant == 3 && dtype != ORC_F32) || op < 0 || op > 1)
+        variant > 6 ||  op < 0 || op > 1)
         return -1;
     prob_t P = { dtype, op, variant, x, y };
     int V = (dtype == ORC_F32) ? 4 : 2;
@@ -235,7 +262,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
     for (int64_t b = 0; b < grid; ++b) {
         for (int t = 0; t < block; ++t) {
             int64_t g = b * block + t;
-            for (int c = 0; c < C; ++c) { ch[c].s = 0.0; ch[c].e = 0.0; }
+            for (int c = 0; c < C; ++c) { ch[c].s = 0.0; ch[c].e = 0.0; ch[c].q = 0; }
             for (int64_t m = 0;; ++m) {
                 int64_t j = g + Pth * m;
                 if (j >= nv) break;
@@ -255,7 +282,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
     pr_t res;
     {
         for (int t = 0; t < block; ++t) {
-            pr_t a = { 0.0, 0.0 };
+            pr_t a = { 0.0, 0.0, 0 };
             if (t < grid) {
                 a = bp[t];
                 for (int64_t i = t + block; i < grid; i += block) a = merge(fg, tw, a, bp[i]);
@@ -299,7 +326,7 @@ static void replay_segment(const cjob_t* J, int64_t s) {
     int64_t a = J->off[s], b = J->off[s + 1];
     size_t osz = (P->dtype == ORC_F64 || J->out_f64) ? 16 : 8;
     void* o = (char*)J->out + osz * (size_t)s;
-    pr_t res = { 0.0, 0.0 };
+    pr_t res = { 0.0, 0.0, 0 };
     if (b > a) {
         int64_t w0 = a / J->tile, w1 = (b - 1) / J->tile;
         int64_t k = w1 - w0 + 1;
@@ -332,7 +359,7 @@ int orc_replay_csr(int dtype, int op, int variant, const void* x, const void* y,
     int V = (dtype == ORC_F32) ? 4 : 2;
     if (!is_pow2(unroll) || unroll > 16 || tile < 32 * V || tile % (32 * V) ||
         nseg < 0 || !off || (dtype != ORC_F32 && dtype != ORC_F64) || variant < 0 ||
-        variant > 6 || (variant == 3 && dtype != ORC_F32) || op < 0 || op > 1)
+        variant > 6 ||  op < 0 || op > 1)
         return -1;
     for (int64_t s = 0; s < nseg; ++s) if (off[s] < 0 || off[s + 1] < off[s]) return -1;
     int64_t next = 0;

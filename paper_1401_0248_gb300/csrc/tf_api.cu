@@ -98,7 +98,7 @@ int64_t csr_grid(const tf_plan& p, int sms) {
     return std::min<int64_t>((int64_t)p.blocks_per_sm * sms, tf::kMaxFlatGrid);
 }
 
-size_t flat_ws_bytes() { return kHeaderBytes + 16 * (size_t)tf::kMaxFlatGrid; }
+size_t flat_ws_bytes() { return kHeaderBytes + tf::kPairBytes * (size_t)tf::kMaxFlatGrid; }
 
 size_t esize(int dtype) { return dtype == 0 ? 4 : 8; }
 
@@ -113,7 +113,6 @@ tf_status common_checks(int op, int dtype, int variant, const void* x, const voi
                         int64_t n, void* out, void* ws, size_t ws_bytes) {
     if (op < 0 || op > 1 || variant < 0 || variant >= kVariants) return TF_ERR_ARG;
     if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
-    if (variant == TF_WIDE && dtype != TF_F32) return TF_ERR_DTYPE;
     if (n < 0 || !out || !ws) return TF_ERR_ARG;
     if (n > 0 && (!x || (op == 1 && !y))) return TF_ERR_ARG;
     const uintptr_t es = esize(dtype);

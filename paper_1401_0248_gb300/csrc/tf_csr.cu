@@ -23,7 +23,7 @@ constexpr int kTfErrOffsets = 6;       // TF_ERR_OFFSETS
 size_t csr_ws_bytes(int64_t n, int64_t nseg) {
     size_t cnt = ((size_t)(nseg > 0 ? nseg : 1) * 4 + 255) / 256 * 256;
     size_t ntiles = (size_t)((n + kMinTile - 1) / kMinTile) + 1;
-    return kHeaderBytes + cnt + ntiles * 2 * 16;
+    return kHeaderBytes + cnt + ntiles * 2 * kPairBytes;
 }
 
 template <typename T, int VAR>
@@ -269,6 +269,7 @@ cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* 
         case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
+        case WIDE: return launch_d<double, WIDE>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case KAHAN: return launch_d<double, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
         case FAST_LIT: return dot ? launch_u<double, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
         case RIG_LIT: return dot ? launch_u<double, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;

@@ -323,14 +323,181 @@ __device__ __forceinline__ bool two_product_i64(double a, double b, double& p, d
     return true;
 }
 
+// ---------------------------------------------------------------- binary128
+// IEEE binary128 in integer arithmetic: the wide ('d') accumulator for
+// binary64 data, the paper's __float128 comparison.  Bits as IEEE stores
+// them: hi = sign | 15-bit exponent (bias 16383) | top 48 fraction bits.
+// Sums of binary64 numbers and products of two never reach the binary128
+// subnormal or overflow ranges, so only zeros, normals, infinities and NaN
+// occur.
+struct q128 {
+    unsigned long long lo, hi;
+    __device__ __forceinline__ q128() : lo(0ull), hi(0ull) {}
+    __device__ __forceinline__ q128(unsigned long long l, unsigned long long h) : lo(l), hi(h) {}
+    __device__ __forceinline__ explicit q128(int) : lo(0ull), hi(0ull) {}   // +0
+    __device__ explicit q128(double x);                                       // exact widening
+};
+typedef unsigned __int128 u128;
+constexpr unsigned long long kQFrac = 0x0000ffffffffffffull;
+
+__device__ __forceinline__ q128 q_pack(unsigned long long sign, int be, u128 m) {
+    // m holds the implicit bit at 112 for normals
+    return q128((unsigned long long)m,
+                (sign << 63) | ((unsigned long long)be << 48) | ((unsigned long long)(m >> 64) & kQFrac));
+}
+
+__device__ __forceinline__ q128::q128(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sign = u >> 63;
+    const int e = (int)((u >> 52) & 0x7ff);
+    unsigned long long f = u & 0x000fffffffffffffull;
+    if (e == 0x7ff) {                                   // Inf / NaN (keep a quiet NaN)
+        hi = (sign << 63) | (0x7fffull << 48) | (f ? (1ull << 47) : 0ull);
+        lo = 0ull;
+    } else if (e == 0) {
+        if (f == 0ull) { hi = sign << 63; lo = 0ull; return; }
+        const int lz = __clzll((long long)f) - 11;        // subnormal binary64: normalise
+        f <<= lz;                                         // leading one at bit 52
+        const q128 r = q_pack(sign, 15361 - lz, (u128)f << 60);      // 2^(-1022 - lz)
+        lo = r.lo; hi = r.hi;
+    } else {
+        const q128 r = q_pack(sign, e + 15360, (u128)(f | (1ull << 52)) << 60);
+        lo = r.lo; hi = r.hi;
+    }
+}
+
+// the exact binary128 product of two binary64 numbers (106-bit significand)
+__device__ __forceinline__ q128 q_mul_exact(double a, double b) {
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
+    const unsigned long long sign = (A ^ B) >> 63;
+    if (ea == 0x7ff || eb == 0x7ff || ea == 0 || eb == 0) {
+        // specials, zeros and subnormals: widen both exactly and multiply the
+        // normalised significands the same way below
+        const q128 qa(a), qb(b);
+        const int xa = (int)((qa.hi >> 48) & 0x7fff), xb = (int)((qb.hi >> 48) & 0x7fff);
+        if (xa == 0x7fff || xb == 0x7fff) {
+            const bool nan = (xa == 0x7fff && ((qa.hi & kQFrac) | qa.lo)) ||
+                             (xb == 0x7fff && ((qb.hi & kQFrac) | qb.lo)) ||
+                             (xa == 0 && xb == 0x7fff) || (xb == 0 && xa == 0x7fff);
+            return nan ? q128(0ull, (0x7fffull << 48) | (1ull << 47))
+                       : q128(0ull, (sign << 63) | (0x7fffull << 48));
+        }
+        if (xa == 0 || xb == 0) return q128(0ull, sign << 63);
+        const u128 ma = ((u128)(qa.hi & kQFrac) << 64 | qa.lo) | ((u128)1 << 112);
+        const u128 mb = ((u128)(qb.hi & kQFrac) << 64 | qb.lo) | ((u128)1 << 112);
+        // both significands are 53-bit values shifted left by 60
+        const u128 P = (ma >> 60) * (mb >> 60);                  // in [2^104, 2^106)
+        const int top = (int)(P >> 105);                         // 1 if bit 105 set
+        return q_pack(sign, xa + xb - 16383 + top, P << (8 - top));
+    }
+    const u128 P = (u128)((A & 0x000fffffffffffffull) | (1ull << 52)) *
+                   (u128)((B & 0x000fffffffffffffull) | (1ull << 52));
+    const int top = (int)(P >> 105);
+    return q_pack(sign, ea + eb - 2046 + 16383 + top, P << (8 - top));
+}
+
+__device__ __forceinline__ int q_clz(u128 m) {
+    const unsigned long long h = (unsigned long long)(m >> 64);
+    return h ? __clzll((long long)h) : 64 + __clzll((long long)(unsigned long long)m);
+}
+
+// a + b rounded to nearest even (three guard bits, sticky folded into the last)
+__device__ __forceinline__ q128 q_add(q128 a, q128 b) {
+    int ea = (int)((a.hi >> 48) & 0x7fff), eb = (int)((b.hi >> 48) & 0x7fff);
+    unsigned long long sa = a.hi >> 63, sb = b.hi >> 63;
+    if (ea == 0x7fff || eb == 0x7fff) {
+        const bool na = ea == 0x7fff && ((a.hi & kQFrac) | a.lo);
+        const bool nb = eb == 0x7fff && ((b.hi & kQFrac) | b.lo);
+        const q128 qnan(0ull, (0x7fffull << 48) | (1ull << 47));
+        if (na || nb) return qnan;
+        if (ea == 0x7fff && eb == 0x7fff) return sa == sb ? a : qnan;
+        return ea == 0x7fff ? a : b;
+    }
+    if (ea == 0) {                                       // a = +-0 (no subnormals occur)
+        if (eb == 0) return q128(0ull, (sa & sb) << 63);  // -0 only for -0 + -0
+        return b;
+    }
+    if (eb == 0) return a;
+    u128 ma = ((u128)(a.hi & kQFrac) << 64 | a.lo) | ((u128)1 << 112);
+    u128 mb = ((u128)(b.hi & kQFrac) << 64 | b.lo) | ((u128)1 << 112);
+    if (ea < eb || (ea == eb && ma < mb)) {             // |a| >= |b|
+        u128 tm = ma; ma = mb; mb = tm;
+        int te = ea; ea = eb; eb = te;
+        unsigned long long ts = sa; sa = sb; sb = ts;
+    }
+    const int d = ea - eb;
+    ma <<= 3;
+    mb <<= 3;
+    if (d > 0) {
+        if (d >= 120) {
+            mb = 1;                                      // sticky only
+        } else {
+            const u128 lost = mb & (((u128)1 << d) - 1);
+            mb = (mb >> d) | (lost ? (u128)1 : (u128)0);
+        }
+    }
+    int e = ea;
+    u128 m;
+    if (sa == sb) {
+        m = ma + mb;
+        if (m >> 116) { m = (m >> 1) | (m & 1); e += 1; }
+    } else {
+        m = ma - mb;
+        if (m == 0) return q128(0ull, 0ull);             // exact cancellation: +0
+        const int lz = q_clz(m) - 12;                    // leading one back to bit 115
+        m <<= lz;
+        e -= lz;
+    }
+    const unsigned int g = (unsigned int)m & 7u;
+    m >>= 3;
+    if (g > 4u || (g == 4u && (m & 1))) {
+        m += 1;
+        if (m >> 113) { m >>= 1; e += 1; }
+    }
+    return q_pack(sa, e, m);
+}
+
+// RN64 of a binary128 value, with gradual underflow and overflow to Inf
+__device__ __forceinline__ double q_to_double(q128 a) {
+    const int e = (int)((a.hi >> 48) & 0x7fff);
+    const unsigned long long sign = a.hi >> 63;
+    if (e == 0x7fff) {
+        const bool nan = (a.hi & kQFrac) | a.lo;
+        return __longlong_as_double((long long)((sign << 63) | (0x7ffull << 52) | (nan ? (1ull << 51) : 0ull)));
+    }
+    if (e == 0) return __longlong_as_double((long long)(sign << 63));
+    const u128 m = ((u128)(a.hi & kQFrac) << 64 | a.lo) | ((u128)1 << 112);
+    const int E = e - 16383;                              // unbiased exponent
+    int sh = 60 + (E < -1022 ? (-1022 - E) : 0);
+    if (sh > 126) return __longlong_as_double((long long)(sign << 63));
+    unsigned long long q = (unsigned long long)(m >> sh);
+    const u128 rem = m & (((u128)1 << sh) - 1);
+    const u128 half = (u128)1 << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) q += 1;
+    unsigned long long bits;
+    if (E < -1022) bits = q;                              // subnormal (2^52 is the least normal)
+    else if (E > 1023) bits = 0x7ffull << 52;             // overflow
+    else bits = ((unsigned long long)(E + 1022) << 52) + q;   // carries into the exponent
+    if (bits >= (0x7ffull << 52)) bits = 0x7ffull << 52;
+    return __longlong_as_double((long long)((sign << 63) | bits));
+}
+
+__device__ __forceinline__ q128 q_neg(q128 a) { return q128(a.lo, a.hi ^ (1ull << 63)); }
+
 // ------------------------------------------------------ accumulation types
 // Chains of the wide variant accumulate binary32 data in binary64; all other
 // variants accumulate in the data type.  Cross-block merges of binary32 data
 // run in binary64 except for the plain variant.
 template <typename T, int VAR> struct Acc { using type = T; };
 template <> struct Acc<float, WIDE> { using type = double; };
+template <> struct Acc<double, WIDE> { using type = q128; };
 template <typename T, int VAR> struct GridAcc { using type = double; };
 template <> struct GridAcc<float, PLAIN> { using type = float; };
+template <> struct GridAcc<double, WIDE> { using type = q128; };
+
+__device__ __forceinline__ q128 add_rn(q128 a, q128 b) { return q_add(a, b); }
 
 template <int VAR> constexpr bool twofold_v = (VAR != PLAIN && VAR != WIDE);
 // the per-item step after the product: literal dots step like the sums
@@ -350,7 +517,10 @@ template <int VAR, bool DOT, typename T, typename A>
 __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
     constexpr int STEP = step_v<VAR>;
     constexpr bool TPROD = DOT && (VAR == FAST || VAR == RIGOROUS);   // TwoProduct error kept
-    if constexpr (VAR == WIDE) {
+    if constexpr (VAR == WIDE && sizeof(T) == 8) {
+        // binary64 data: binary128 accumulator, products exact in binary128
+        s = q_add(s, DOT ? q_mul_exact(a, b) : q128(a));
+    } else if constexpr (VAR == WIDE) {
         double p;
         if constexpr (DOT) {
             if (!wide_product_i(a, b, p)) p = wide_product_slow(a, b);
@@ -434,6 +604,12 @@ __device__ __forceinline__ void merge(A& v, A& e, A v2, A e2) {
     }
 }
 
+template <typename A>
+__device__ __forceinline__ A shfl_xor(A v, int o) { return __shfl_xor_sync(FULL, v, o); }
+__device__ __forceinline__ q128 shfl_xor(q128 v, int o) {
+    return q128(__shfl_xor_sync(FULL, v.lo, o), __shfl_xor_sync(FULL, v.hi, o));
+}
+
 // xor butterfly over the lanes of a warp for offsets o = W/2 ... 1; every
 // lane holds lane (lane ^ o)'s previous pair as second operand.
 template <bool TW, typename A>
@@ -441,8 +617,8 @@ __device__ __forceinline__ void warp_fold(A& v, A& e, int W = 32) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         if (o < W) {
-            A v2 = __shfl_xor_sync(FULL, v, o);
-            A e2 = __shfl_xor_sync(FULL, e, o);
+            A v2 = shfl_xor(v, o);
+            A e2 = shfl_xor(e, o);
             merge<TW>(v, e, v2, e2);
         }
     }
@@ -487,11 +663,16 @@ __device__ __forceinline__ void ld_vec(const T* p, bool aligned, T (&r)[V]) {
     }
 }
 
-// coherent 16-byte load of a pair written by another block (bypasses L1)
+// coherent load of a pair written by another block (bypasses L1)
 template <typename A>
 __device__ __forceinline__ void ld_pair_cg(const A* p, A& v, A& e) {
     v = __ldcg(p);
     e = __ldcg(p + 1);
+}
+__device__ __forceinline__ void ld_pair_cg(const q128* p, q128& v, q128& e) {
+    const unsigned long long* u = reinterpret_cast<const unsigned long long*>(p);
+    v = q128(__ldcg(u), __ldcg(u + 1));
+    e = q128(__ldcg(u + 2), __ldcg(u + 3));
 }
 
 // ------------------------------------------------------------- workspace
@@ -510,7 +691,13 @@ constexpr size_t kWsHeader = 256;
 // binary32 twofold / wide: v = RN32(V), e = RN32((V - v) + E).
 template <typename T, int VAR, typename G>
 __device__ __forceinline__ void write_out(void* out, int64_t idx, G V, G E, bool out_f64) {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (sizeof(G) == 16) {
+        // binary128 accumulator: (RN64(S), RN64(S - RN64(S)))
+        double* o = (double*)out;
+        const double hi = q_to_double(V);
+        o[2 * idx] = hi;
+        o[2 * idx + 1] = q_to_double(q_add(V, q_neg(q128(hi))));
+    } else if constexpr (sizeof(T) == 8) {
         double* o = (double*)out;
         o[2 * idx] = V; o[2 * idx + 1] = E;
     } else {

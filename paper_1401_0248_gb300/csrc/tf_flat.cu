@@ -153,6 +153,7 @@ cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void*
         case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
+        case WIDE: return launch_d<double, WIDE>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case KAHAN: return launch_d<double, KAHAN>(dot, unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st);
         case FAST_LIT: return dot ? launch_u<double, FAST_LIT, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st) : cudaErrorInvalidValue;
         case RIG_LIT: return dot ? launch_u<double, RIG_LIT, true>(unroll, x, y, n, out, ws, block, grid, aligned, out_f64, st) : cudaErrorInvalidValue;

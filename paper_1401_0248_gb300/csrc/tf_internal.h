@@ -11,6 +11,7 @@ namespace tf {
 constexpr size_t kHeaderBytes = 256;
 constexpr int64_t kMinTile = 1024;       // smallest batched tile, in elements
 constexpr int64_t kMaxFlatGrid = 8 * 256; // blocks_per_sm <= 8, SM count <= 256
+constexpr size_t kPairBytes = 32;         // one (value, error) slot: two binary128 at most
 
 // single-vector reduction: dtype 0 f32 / 1 f64, variant 0..3, dot 0/1
 cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void* x,

@@ -57,7 +57,6 @@ extern "C" tf_status tf_sum_noalloc(const void* x, int64_t n, tf_dtype dtype,
                                     tf_stream_t stream) {
     if (variant < TF_PLAIN || variant > TF_KAHAN) return TF_ERR_ARG;
     if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
-    if (variant == TF_WIDE && dtype != TF_F32) return TF_ERR_DTYPE;
     if (n < 0 || !out || (n > 0 && !x)) return TF_ERR_ARG;
     const uintptr_t es = dtype == TF_F32 ? 4 : 8;
     if ((uintptr_t)x % es || (uintptr_t)out % ((flags & TF_OUT_F64) ? 8 : es)) return TF_ERR_ALIGN;
@@ -67,6 +66,8 @@ extern "C" tf_status tf_sum_noalloc(const void* x, int64_t n, tf_dtype dtype,
     tf_status s = tf_launch_shape(TF_OP_SUM, 0, dtype, variant, n, &block, &unroll, &grid, &tile);
     if (s != TF_OK) return s;
     if (grid > kNoallocMaxBlocks) return TF_ERR_UNSUPPORTED;   // scratch holds 2048 blocks
+    // a binary128 accumulator ('wide' binary64) needs two 16-byte slots per block
+    if (dtype == TF_F64 && variant == TF_WIDE && grid > kNoallocMaxBlocks / 2) return TF_ERR_UNSUPPORTED;
 
     void* scratch = nullptr;
     if ((s = noalloc_scratch(&scratch)) != TF_OK) return s;

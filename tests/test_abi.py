@@ -54,7 +54,7 @@ def test_host_side_checks_without_gpu():
     assert L.tf_workspace_size(0, 1, 0, 1, 1 << 24, 100, C.byref(b)) == 0 and b.value > big
     # argument errors come back before any device work
     assert L.tf_sum(None, -1, 0, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 1
-    assert L.tf_sum(None, 10, 1, 3, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 2  # wide f64
+    assert L.tf_sum(None, 10, 7, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 2  # no such dtype
     assert L.tf_sum(C.c_void_p(2), 10, 0, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 4
     assert L.tf_sum(C.c_void_p(256), 10, 0, 1, C.c_void_p(256), C.c_void_p(256), 16, 0, None) == 3
     p = twofold.Plan(100, 2, 2, 0)

@@ -197,8 +197,6 @@ def check_flat(op, variant, dt, x, y, out_f64=False):
 @pytest.mark.parametrize("op,variant", VARIANTS + [("sum", "wide"), ("dot", "wide")])
 @pytest.mark.parametrize("n", SIZES)
 def test_flat_bit_exact_vs_replay(dt, op, variant, n):
-    if variant == "wide" and dt == "f64":
-        pytest.skip("wide is defined for binary32 data only")
     x = I.normal(n, dt, seed=n % 4000, device=DEV)
     y = I.normal(n, dt, seed=n % 4000, stream=3, device=DEV) if op == "dot" else None
     out, (block, unroll, grid) = check_flat(op, variant, dt, x, y)
@@ -221,6 +219,32 @@ def test_flat_ill_conditioned_bit_exact(dt, cond):
     for variant in ("fast", "rigorous", "plain"):
         check_flat("sum", variant, dt, ic.x, None)
         check_flat("dot", variant, dt, icd.x, icd.y)
+
+
+def test_flat_wide_f64_binary128_special_values_bit_exact():
+    """binary64 data in the binary128 accumulator: zeros, subnormals, huge
+    values, and Inf/NaN propagation"""
+    rng = np.random.default_rng(21)
+    n = 100003
+    x = rng.standard_normal(n) * 10.0 ** rng.integers(-300, 300, size=n)
+    y = rng.standard_normal(n) * 10.0 ** rng.integers(-300, 300, size=n)
+    x[::7] = 0.0
+    x[1::11] = -0.0
+    x[2::13] = 5e-324
+    y[3::17] = -2.5e-310
+    tx, ty = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
+    check_flat("sum", "wide", "f64", tx, None)
+    check_flat("dot", "wide", "f64", tx, ty)
+    # exactness where every partial sum fits in 113 bits: integers
+    xi = torch.from_numpy(rng.integers(-2 ** 50, 2 ** 50, size=n).astype(np.float64)).to(DEV)
+    out = _np(tf.sum(xi, "wide"))
+    ex = O.exact(_np(xi))
+    assert out[0] == ex.s and out[1] == ex.s_lo
+    xs = x.copy()
+    xs[5] = np.inf
+    check_flat("sum", "wide", "f64", torch.from_numpy(xs).to(DEV), None)
+    xs[6] = -np.inf
+    check_flat("sum", "wide", "f64", torch.from_numpy(xs).to(DEV), None)
 
 
 def test_flat_wide_special_values_bit_exact():
@@ -394,8 +418,6 @@ def check_csr(op, variant, dt, x, y, off_h, out_f64=False):
 @pytest.mark.parametrize("dt", ["f32", "f64"])
 @pytest.mark.parametrize("op,variant", VARIANTS + [("sum", "wide"), ("dot", "wide")])
 def test_csr_bit_exact_vs_replay(dt, op, variant):
-    if variant == "wide" and dt == "f64":
-        pytest.skip("wide is defined for binary32 data only")
     off_h = make_csr(300, 1, 20000, seed=5, empties=(0, 7, 8, 299))
     n = int(off_h[-1]) + 5                      # x longer than the segments cover
     x = I.normal(n, dt, seed=6, device=DEV)

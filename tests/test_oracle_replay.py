@@ -273,3 +273,165 @@ def test_replay_csr_segments_independent_and_empty():
     D = 512 // 64 + 2 + 5 + (xx.size // 512) // 32 + 5
     g = D * u / (1 - D * u)
     assert abs(r.r) <= u * abs(r.s) + g * g * r.sabs
+
+
+# --------------------------------------------- binary128 accumulator ('wide' f64)
+def rn113(f):
+    """round a Fraction to the nearest binary128 number (ties to even); the
+    values here stay far inside binary128's normal range"""
+    from fractions import Fraction
+    if f == 0:
+        return Fraction(0)
+    a = abs(f)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    scale = Fraction(2) ** (e - 112)
+    q, r = divmod(a / scale, 1)
+    q = int(q)
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and q & 1):
+        q += 1
+    return (q * scale) if f > 0 else -(q * scale)
+
+
+class QArith:
+    """binary128 accumulation: every add rounds once to 113 bits"""
+    def merge(self, a, b):
+        return rn113(a + b)
+
+    def butterfly(self, vals):
+        return Arith.butterfly(self, vals)
+
+    def tree(self, ch):
+        return Arith.tree(self, ch)
+
+
+def chain_q(x, y, idx):
+    from fractions import Fraction
+    s = Fraction(0)
+    for i in idx:
+        t = Fraction(float(x[i])) * (Fraction(float(y[i])) if y is not None else 1)
+        s = rn113(s + t)
+    return s
+
+
+def out_q(S):
+    from fractions import Fraction
+    v = float(S)                       # int/int true division: correctly rounded
+    return np.array([v, float(S - Fraction(v))], dtype=np.float64)
+
+
+def compose_flat_q(x, y, block, unroll, grid):
+    """compose_flat's order with binary128 chains and folds"""
+    from fractions import Fraction
+    V, n, P = 2, x.size, grid * block
+    nv, tail = n // V, n % V
+    q, C = QArith(), unroll * 2
+    bps = []
+    for b in range(grid):
+        tps = []
+        for t in range(block):
+            g = b * block + t
+            lists = [[] for _ in range(C)]
+            m = 0
+            while g + P * m < nv:
+                for l in range(V):
+                    lists[(m % unroll) * V + l].append((g + P * m) * V + l)
+                m += 1
+            if tail and g == nv % P:
+                lists[((nv // P) % unroll) * V].append(nv * V)
+            tps.append(q.tree([chain_q(x, y, li) for li in lists]))
+        wps = [q.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
+        bps.append(q.butterfly(wps))
+    tps = []
+    for t in range(block):
+        a = Fraction(0)
+        if t < grid:
+            a = bps[t]
+            for i in range(t + block, grid, block):
+                a = q.merge(a, bps[i])
+        tps.append(a)
+    wps = [q.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
+    return out_q(q.butterfly(wps))
+
+
+@pytest.mark.parametrize("op,n,block,unroll,grid", [
+    ("sum", 1001, 32, 2, 3), ("dot", 777, 64, 1, 2), ("sum", 2, 32, 4, 1),
+    ("dot", 1537, 32, 4, 5)])
+@pytest.mark.parametrize("cond", [None, 1e28])
+def test_replay_flat_binary128_matches_composition(op, n, block, unroll, grid, cond):
+    if cond is not None and n < 3:
+        pytest.skip("the ill-conditioned generator needs three elements")
+    if cond is None:
+        x = I.normal(n, "f64", seed=n + 11).numpy()
+        x = x * np.exp2(np.arange(n) % 97 - 48.0)      # wide dynamic range
+        y = I.normal(n, "f64", seed=n + 11, stream=5).numpy() if op == "dot" else None
+    else:
+        # cancellation far beyond 113 bits: the result depends on the order
+        ic = I.ill_conditioned(n, "f64", cond, seed=n, dot=op == "dot")
+        x, y = ic.x.numpy(), (ic.y.numpy() if op == "dot" else None)
+    want = compose_flat_q(x, y, block, unroll, grid)
+    got = O.replay_flat(op, "wide", x, y, block=block, unroll=unroll, grid=grid)
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (got, want)
+
+
+def test_replay_binary128_exact_and_bounded():
+    """integer data below 2^60 sums exactly in 113 bits; otherwise the pair
+    obeys the recursive-summation bound in binary128 plus the output rounding"""
+    rng = np.random.default_rng(4)
+    xi = rng.integers(-2 ** 52, 2 ** 52, size=50001).astype(np.float64)
+    got = O.replay_flat("sum", "wide", xi, block=128, unroll=2, grid=9)
+    r = O.exact(xi)
+    assert got[0] == r.s and got[1] == r.s_lo
+    # 2^60 + 1 - 2^60 is lost by a binary64 sum and kept by binary128
+    got = O.replay_flat("sum", "wide", np.array([2.0 ** 60, 1.0, -2.0 ** 60]),
+                        block=32, unroll=1, grid=1)
+    assert got[0] == 1.0 and got[1] == 0.0
+    ic = I.ill_conditioned(1 << 15, "f64", 1e25, seed=5)
+    x = ic.x.numpy()
+    got = O.replay_flat("sum", "wide", x, block=64, unroll=2, grid=4)
+    r = O.exact(x, v=float(got[0]), e=float(got[1]))
+    u = 2.0 ** -113
+    D = depth(x.size, 2, 64, 2, 4)
+    assert abs(r.r) <= 2.0 ** -105 * abs(r.s) + D * u / (1 - D * u) * r.sabs
+
+
+def test_replay_csr_binary128_matches_composition():
+    """compose_csr's tile order with binary128 chains and folds"""
+    from fractions import Fraction
+    L = I.csr_lengths(12, 3, 400, seed=15)
+    L[4] = 0
+    off = I.csr_offsets(L)
+    n, unroll, tile = int(off[-1]), 2, 64
+    ic = I.ill_conditioned(n, "f64", 1e28, seed=16)
+    x = ic.x.numpy()
+    q = QArith()
+    want = []
+    for s in range(off.size - 1):
+        a, b = int(off[s]), int(off[s + 1])
+        pcs = []
+        for w in range(a // tile, (b - 1) // tile + 1) if b > a else []:
+            lo, hi = max(a, w * tile), min(b, (w + 1) * tile)
+            lists = [[[] for _ in range(unroll * 2)] for _ in range(32)]
+            for i in range(lo, hi):
+                r = i - w * tile
+                lists[(r // 2) % 32][((r // 64) % unroll) * 2 + r % 2].append(i)
+            pcs.append(q.butterfly([q.tree([chain_q(x, None, li) for li in lists[l]])
+                                    for l in range(32)]))
+        if not pcs:
+            res = Fraction(0)
+        elif len(pcs) == 1:
+            res = pcs[0]
+        else:
+            lanes = []
+            for l in range(32):
+                acc = Fraction(0)
+                if l < len(pcs):
+                    acc = pcs[l]
+                    for i in range(l + 32, len(pcs), 32):
+                        acc = q.merge(acc, pcs[i])
+                lanes.append(acc)
+            res = q.butterfly(lanes)
+        want.append(out_q(res))
+    got = O.replay_csr("sum", "wide", x, off, unroll=unroll, tile=tile)
+    assert np.array_equal(got.view(np.uint8), np.array(want).view(np.uint8))
