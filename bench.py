@@ -39,6 +39,8 @@ import sys
 import time
 from fractions import Fraction
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -52,17 +54,21 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 PLANS_PATH = os.path.join(ROOT, "paper_1401_0248_gb300", "plans_gb300.txt")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0
 
 # Binary64-pipe instructions per element that the binary64 kernels issue:
 # the twofold steps keep two roundings on the binary64 pipe (t = s + p and
 # e = e + y; dots also q + ep) and compute the exact error terms and the
-# product on the integer pipe; plain keeps its add (and multiply).
+# product on the integer pipe; plain keeps its add (and multiply).  The sums
+# issue their adds as DFMA by 1.0 (the faster binary64 instruction on GB300),
+# the dots as DADD; each is held against its own measured rate.
 FP64_PIPE_OPS = {("sum", "plain"): 1, ("sum", "fast"): 2, ("sum", "rigorous"): 2,
                  ("dot", "plain"): 2, ("dot", "fast"): 3, ("dot", "rigorous"): 3}
 # the paper's operation counts (Examples 1 and 3; dots add TwoProduct and one add)
 PAPER_OPS = {("sum", "plain"): 1, ("sum", "fast"): 4, ("sum", "rigorous"): 7,
              ("dot", "plain"): 2, ("dot", "fast"): 7, ("dot", "rigorous"): 10}
 FALLBACK_DADD_GOPS = 528.0   # binary64 adds/s of a GB300 (1.67/clk/SM at 2.07 GHz)
+FALLBACK_DFMA_GOPS = 626.0   # binary64 fused multiply-adds/s (2/clk/SM at 2.07 GHz)
 
 
 def kernel_sources_hash(files=("tf_device.cuh", "tf_flat.cu")):
@@ -316,15 +322,19 @@ def run_gpu(args, rank, world, local):
     total_bytes = sum_over_ranks(step_bytes, world)
     value = total_bytes / (step_ms * 1e-3) / 1e9
 
-    # per-kernel report and accuracy
+    # per-kernel report and accuracy: fractions of the measured copy rate, of
+    # the measured two-array read rate (probe) and of the nominal 7.9 TB/s
     hbm, peak_kind = load_peaks()
+    read_bw = (probes or {}).get("read2_gbs")
     kernels, accuracy = {}, {}
     for k in ks_all:
         dt, cond, op, v, _ = k
         ms = kern_ms.get(k, base_ms.get(k))
         gbs = nbytes(dt, op, n) / (ms * 1e-3) / 1e9
         name = "%s_%s_%s_c%g" % (dt, op, v, cond)
-        kernels[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4)}
+        kernels[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
+                         "frac_read": round(gbs / read_bw, 4) if read_bw else None,
+                         "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
         _, _, S, cond_got = data[(dt, cond)][op]
         o = outs[k].cpu().tolist()
         acc = {"cond": float("%.3g" % cond_got), "rel_err_v_plus_e": rel_err(S, o[0], o[1]),
@@ -333,6 +343,22 @@ def run_gpu(args, rank, world, local):
             rv = S - Fraction(float(o[0]))
             acc["e_over_residual"] = (float(Fraction(float(o[1])) / rv) if rv != 0 else None)
         accuracy[name] = acc
+
+    # how well e estimates the value's own error: rho = e / (S - v) over the
+    # step's twofold results
+    rhos = [a["e_over_residual"] for a in accuracy.values() if a.get("e_over_residual") is not None]
+    nz = [r for r in rhos if r != 0.0]
+    zero_ok = [float(Fraction(float(outs[k].cpu()[1]))) == 0.0 for k in step_ks
+               if data[(k[0], k[1])][k[2]][2] == Fraction(float(outs[k].cpu()[0]))]
+    e_tracking = {
+        "n": len(rhos),
+        "median_abs_log2_rho": round(statistics.median(abs(math.log2(abs(r))) for r in nz), 6)
+        if nz else None,
+        "n_e_zero_with_residual": len(rhos) - len(nz),
+        "frac_rho_in_half_to_2": round(sum(0.5 <= r <= 2.0 for r in rhos) / len(rhos), 4)
+        if rhos else None,
+        "e_zero_where_value_exact": (all(zero_ok) if zero_ok else None, len(zero_ok)),
+    }
 
     # roofline of the kernel with the largest share of the step
     dom = max(step_ks, key=lambda k: kern_ms[k])
@@ -350,14 +376,19 @@ def run_gpu(args, rank, world, local):
         pass
     bytes_dom = nbytes(dt, op, n)
     if dt == "f64":
-        # bound by the binary64 pipe: its issued adds against the measured add rate
-        peak_ops = (probes or {}).get("dadd_gops") or FALLBACK_DADD_GOPS
+        # bound by the binary64 pipe: its issued adds against the measured rate
+        # of the instruction they use (DFMA by 1.0 for sums, DADD for dots)
+        fma_adds = op == "sum"
+        peak_ops = (probes or {}).get("dadd_as_fma_reg_gops" if fma_adds else "dadd_gops") \
+            or (FALLBACK_DFMA_GOPS if fma_adds else FALLBACK_DADD_GOPS)
         ops = FP64_PIPE_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": round(ops, 1), "peak": round(peak_ops, 1),
                     "unit": "G binary64-pipe ops/s", "frac": round(ops / peak_ops, 4),
                     "traffic": traffic, "kernel": dom_name,
-                    "peak_source": "measured binary64 add rate (probe kind 1) on this GPU"
-                                   if probes else "fallback 528 G/s",
+                    "peak_source": ("measured rate of binary64 adds issued as DFMA by a runtime "
+                                    "1.0 (probe kind 13) on this GPU" if fma_adds else
+                                    "measured binary64 add rate (probe kind 1) on this GPU")
+                                   if probes else "fallback (no probes)",
                     "paper_ops_per_s_g": round(PAPER_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9, 1),
                     "hbm_gbs": round(bytes_dom / (dom_ms * 1e-3) / 1e9, 1),
                     "hbm_frac": round(bytes_dom / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
@@ -382,6 +413,7 @@ def run_gpu(args, rank, world, local):
         "roofline": roofline,
         "kernels": kernels,
         "accuracy": accuracy,
+        "e_tracking": e_tracking,
         "probes": probes,
     }
     return result, data, ws, outs, ks_all, step_ks
@@ -423,6 +455,76 @@ def run_probes(data, dev, stream, cond0):
         ops = tf.ALU_OPS_PER_ITER[tf.ALU_KINDS[kind]] * iters * blocks * threads
         out[kind + "_gops"] = round(ops / (a.elapsed_time(e) * 1e-3) / 1e9, 1)
     return out
+
+
+def run_small(dev, stream, reps=20):
+    """The L2-resident case: N = 2^20 binary64 (8 MiB per operand), uniform
+    [-1, 1).  Launches are replayed from CUDA graphs so that the host's call
+    overhead is not timed: hot = `reps` launches back to back; flushed =
+    `reps` launches each after writing a 256 MiB buffer (larger than L2),
+    minus the same graph without the launches."""
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    from paper_1401_0248_gb300 import twofold as tf
+    n = 1 << 20
+    x = I.uniform(n, "f64", seed=0, stream=0, device=dev)
+    y = I.uniform(n, "f64", seed=0, stream=1, device=dev)
+    ws = torch.zeros(tf.workspace_size("dot", False, torch.float64, "rigorous", n),
+                     dtype=torch.uint8, device=dev)
+    out = torch.empty(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
+
+    def graph_ms(body, replays=5):
+        body()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream(device=dev)
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            with torch.cuda.graph(g, stream=gs):
+                body()
+        torch.cuda.synchronize()
+        g.replay()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(replays):
+            g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        del g
+        return a.elapsed_time(b) / replays
+
+    def flushes():
+        for _ in range(reps):
+            flush.fill_(1)
+    t_flush = graph_ms(flushes)
+    res = {"config": "N=2^20 f64, uniform [-1, 1); CUDA-graph replay", "kernels": {}}
+    for op in OPS:
+        for v in TWOFOLD + ("plain",):
+            def call():
+                if op == "sum":
+                    tf.sum(x, v, out=out, ws=ws)
+                else:
+                    tf.dot(x, y, v, out=out, ws=ws)
+
+            def hot_body():
+                for _ in range(reps):
+                    call()
+
+            def cold_body():
+                for _ in range(reps):
+                    flush.fill_(1)
+                    call()
+            hot = graph_ms(hot_body) / reps
+            cold = max(graph_ms(cold_body) - t_flush, 0.0) / reps
+            byts = nbytes("f64", op, n)
+            res["kernels"]["f64_%s_%s" % (op, v)] = {
+                "hot_us": round(hot * 1e3, 2), "hot_gbs": round(byts / (hot * 1e-3) / 1e9, 1),
+                "flushed_us": round(cold * 1e3, 2),
+                "flushed_gbs": round(byts / (cold * 1e-3) / 1e9, 1) if cold > 0 else None}
+    del flush
+    return res
 
 
 def run_batched(args, dev, stream):
@@ -587,11 +689,27 @@ def host_sample(data, m):
 
 
 def run_cpu_baseline(data, m):
-    b, s = cpu_oracle_step(host_sample(data, m), m)
+    import oracle as O
+    hs = host_sample(data, m)
+    b, s = cpu_oracle_step(hs, m)
+    el = sum(min(m, x.size) for x, _ in hs.values()) * len(TWOFOLD)
+    # context: the exact superaccumulator on all host cores, and the paper's
+    # binary128 ('d' for double) loop on one core, on the f64 cond-1e8 sample
+    x = hs[("f64", 1e8, "sum")][0] if ("f64", 1e8, "sum") in hs else next(iter(hs.values()))[0]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.exact(x, nthreads=cores)
+    t_ex = time.perf_counter() - t0
+    extra = {"exact_superaccumulator_elem_s": round(x.size / t_ex, 1), "exact_cores": cores}
+    if x.dtype == np.float64:
+        t0 = time.perf_counter()
+        O.loop("sumq", x)
+        t_q = time.perf_counter() - t0
+        extra["sumq_f64_gbs_one_core"] = round(x.nbytes / t_q / 1e9, 4)
     return {"value": round(b / s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": "first %d elements of each of the step's 24 inputs, the oracle's "
                       "sequential twofold loops (one host thread, as in the paper)" % m,
-            "seconds": round(s, 2)}
+            "seconds": round(s, 2), "elem_s": round(el / s, 1), "context": extra}
 
 
 def run_reference(args, rank, world):
@@ -662,6 +780,8 @@ def main(argv=None):
     if not args.no_batched:
         res["batched"] = run_batched(args, torch.device("cuda", local),
                                      torch.cuda.current_stream(torch.device("cuda", local)))
+        res["small"] = run_small(torch.device("cuda", local),
+                                 torch.cuda.current_stream(torch.device("cuda", local)))
     if not args.no_e2e:
         e2e = run_e2e(args, data, ws, step_ks, torch.device("cuda", local))
         e2e["value"] = round(sum_over_ranks(e2e["value"], world), 2) if world > 1 else e2e["value"]

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtwofold.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["tf_flat.cu", "tf_csr.cu", "tf_aux.cu", "tf_api.cu", "tf_noalloc.cu"]
+SOURCES = ["tf_flat.cu", "tf_csr.cu", "tf_csr_tma.cu", "tf_aux.cu", "tf_api.cu", "tf_noalloc.cu"]
 HEADERS = ["tf_device.cuh", "tf_internal.h"]
 
 NVCC_FLAGS = [

@@ -2,39 +2,42 @@
 // persistent launch (sm_103a).
 //
 // Load balance does not depend on the length mix: the concatenated vector is
-// cut into equal tiles of `tile` elements, and each warp of the persistent
-// grid takes a contiguous run of tiles.  Inside a tile the warp reduces each
+// cut into equal tiles of `tile` elements, and the warps of the persistent
+// grid take tiles from a per-call counter in increasing order (one atomic per
+// tile), so all warps stream one moving window of the input and finish
+// within one tile of each other.  Inside a tile the warp reduces each
 // segment's piece: lane l takes the 16-byte vector slots l, l+32, ... of the
-// tile, slot m-th for the lane feeding chains (m mod U)*V + (element mod V).
-// Elements outside the piece are fed as +0, which leaves a twofold, plain or
-// wide chain's bits unchanged (Kahan chains skip them), so the chain
-// assignment is the documented one with no branches in the streaming loop.  A segment inside one tile is written directly; a
+// tile, slot m feeding chains (m mod U)*V + (element mod V).  Elements
+// outside the piece are fed as +0, which leaves a twofold, plain or wide
+// chain's bits unchanged (Kahan chains skip them), so the chain assignment is
+// the documented one.  A segment inside one tile is written directly; a
 // segment over k tiles leaves k piece pairs in the workspace and the warp that
 // completes the k-th piece (a per-segment ticket, no waiting) merges them in
-// tile order.  A first small kernel checks the offsets, clears the tickets
-// and writes the empty segments.
-#include "tf_device.cuh"
-#include "tf_internal.h"
+// tile order, so which warp reduces which tile never changes a bit.  A first
+// small kernel checks the offsets, clears the tickets, writes the empty
+// segments and records the segment holding each tile's first element.
+#include "tf_csr.cuh"
 
 namespace tf {
 
 constexpr int kTfErrOffsets = 6;       // TF_ERR_OFFSETS
 
 size_t csr_ws_bytes(int64_t n, int64_t nseg) {
-    size_t cnt = ((size_t)(nseg > 0 ? nseg : 1) * 4 + 255) / 256 * 256;
-    size_t ntiles = (size_t)((n + kMinTile - 1) / kMinTile) + 1;
-    return kHeaderBytes + cnt + ntiles * 2 * kPairBytes;
+    const size_t ntiles = csr_max_tiles(n);
+    return kHeaderBytes + csr_cnt_bytes(nseg) + ntiles * 2 * kPairBytes + ntiles * 8;
 }
 
 template <typename T, int VAR>
 __global__ void csr_prepare(const int64_t* __restrict__ off, int64_t nseg, int64_t n,
-                            void* __restrict__ out, unsigned char* __restrict__ ws, int out_f64) {
+                            int64_t tile, void* __restrict__ out, unsigned char* __restrict__ ws,
+                            int64_t* __restrict__ tile_seg, int out_f64) {
     using G = typename GridAcc<T, VAR>::type;
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool bad = false;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= nseg; s += stride) {
+    for (int64_t s = first; s <= nseg; s += stride) {
         const int64_t a = off[s];
         bad |= (a < 0) || (a > n) || (s == 0 && a != 0);
         if (s < nseg) {
@@ -43,6 +46,19 @@ __global__ void csr_prepare(const int64_t* __restrict__ off, int64_t nseg, int64
             cnt[s] = 0u;
             if (b == a) write_out<T, VAR, G>(out, s, G(0), G(0), out_f64 != 0);
         }
+    }
+    // the segment holding element t*tile: the last s < nseg with off[s] <= t*tile
+    // (indices stay in [0, nseg] whatever the offsets hold; with invalid
+    // offsets the map is not used)
+    const int64_t ntiles = (n + tile - 1) / tile;
+    for (int64_t t = first; t < ntiles; t += stride) {
+        const int64_t pos = t * tile;
+        int64_t lo = 0, hi = nseg;
+        while (hi - lo > 1) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (off[mid] <= pos) lo = mid; else hi = mid;
+        }
+        tile_seg[t] = lo;
     }
     if (bad) {
         atomicExch(&hdr->call_bad, 1);
@@ -54,17 +70,25 @@ template <typename T, int VAR, bool DOT, int U>
 __global__ void __launch_bounds__(512)
 csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __restrict__ off,
            int64_t nseg, void* __restrict__ out, unsigned char* __restrict__ ws,
-           size_t cnt_bytes, int64_t tile, int aligned, int out_f64) {
+           size_t cnt_bytes, const int64_t* __restrict__ tile_seg, int64_t tile, int aligned,
+           int out_f64) {
     using A = typename Acc<T, VAR>::type;
     using G = typename GridAcc<T, VAR>::type;
     constexpr bool TW = twofold_v<VAR>;
     constexpr int V = 16 / sizeof(T);
     constexpr int C = U * V;
+    constexpr int SV = 32 * V;              // elements per warp-wide slot row
+    // binary32 data streams at the memory's pace: load the next full step
+    // while the current one is fed (the binary64 and wide kernels are bound
+    // by their arithmetic and keep the registers instead)
+    constexpr bool PREFETCH = sizeof(T) == 4 && VAR != WIDE;
 
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     G* pieces = reinterpret_cast<G*>(ws + kWsHeader + cnt_bytes);
     const int lane = threadIdx.x & 31;
+    double one = 1.0;                 // binary64 sums: a 1.0 the compiler cannot see
+    if constexpr (sizeof(T) == 8 && !DOT) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const bool bad = *reinterpret_cast<volatile int*>(&hdr->call_bad) != 0;
     if (bad) {
@@ -75,145 +99,139 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
     } else {
         const int64_t total = off[nseg];
         const int64_t ntiles = (total + tile - 1) / tile;
-        const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-        const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        const int64_t t0 = ntiles * gw / nw, t1 = ntiles * (gw + 1) / nw;
-        if (t0 < t1) {
-            // segment holding element t0*tile: the last s < nseg with off[s] <= pos
-            int64_t s = 0;
-            if (lane == 0) {
-                const int64_t pos = t0 * tile;
-                int64_t lo = 0, hi = nseg;
-                while (hi - lo > 1) {
-                    const int64_t mid = lo + (hi - lo) / 2;
-                    if (off[mid] <= pos) lo = mid; else hi = mid;
-                }
-                s = lo;
-            }
-            s = __shfl_sync(FULL, s, 0);
-            int64_t a = off[s], b = off[s + 1];
-            for (int64_t t = t0; t < t1; ++t) {
-                const int64_t tlo = t * tile;
-                const int64_t thi = min(tlo + tile, total);
-                for (;;) {
-                    const int64_t pa = max(a, tlo), pb = min(b, thi);
-                    if (pb > pa) {
-                        // ---- the piece [pa, pb) of segment s in tile t
-                        A cs[C], ce[C];
+        unsigned long long t = 0ull;
+        if (lane == 0) t = atomicAdd(&hdr->tile_next, 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        while ((int64_t)t < ntiles) {
+            // claim the next tile now; the answer is needed only after this one
+            unsigned long long tn = 0ull;
+            if (lane == 0) tn = atomicAdd(&hdr->tile_next, 1ull);
+            const int64_t tlo = (int64_t)t * tile;
+            const int64_t thi = min(tlo + tile, total);
+            int64_t s = __ldg(tile_seg + t);
+            int64_t a = __ldg(off + s), b = __ldg(off + s + 1);
+            for (;;) {
+                const int64_t pa = max(a, tlo), pb = min(b, thi);
+                if (pb > pa) {
+                    // ---- the piece [pa, pb) of segment s in tile t
+                    A cs[C], ce[C];
 #pragma unroll
-                        for (int c = 0; c < C; ++c) { cs[c] = A(0); ce[c] = A(0); }
-                        const int64_t qa = (pa - tlo) / V, qb = (pb - 1 - tlo) / V;
-                        const int64_t mlo = qa > lane ? (qa - lane + 31) / 32 : 0;
-                        const int64_t mhi = qb >= lane ? (qb - lane) / 32 : -1;
-                        for (int64_t mb = (mlo / U) * U; mb <= mhi; mb += U) {
-                            T xv[U][V], yv[U][V];
-                            // Kahan chains skip the slots outside the piece (a +0 item
-                            // would apply their pending compensation); every other
-                            // variant takes them as +0, which leaves its bits unchanged
-                            unsigned int live = ~0u;
-                            // slot addresses grow with m, so the step's U vectors all lie
-                            // inside the piece iff its first and last ones do
-                            const int64_t b0 = tlo + (lane + 32 * mb) * V;
-                            const int64_t b1 = b0 + (int64_t)(32 * V) * (U - 1);
-                            if (mb >= mlo && mb + (U - 1) <= mhi && b0 >= pa && b1 + V <= pb) {
+                    for (int c = 0; c < C; ++c) { cs[c] = A(0); ce[c] = A(0); }
+                    // this lane's slots m touching the piece: [mlo, mhi]; lying
+                    // wholly inside it: [mA, mB] (tile-relative, 32-bit: tile <= 2^22)
+                    const int ra = (int)(pa - tlo), rb = (int)(pb - tlo);
+                    const int qa = ra / V, qb = (rb - 1) / V;
+                    const int mlo = qa > lane ? (qa - lane + 31) / 32 : 0;
+                    const int mhi = qb >= lane ? (qb - lane) / 32 : -1;
+                    const int da = ra - lane * V, db = rb - V - lane * V;
+                    const int mA = da > 0 ? (da + SV - 1) / SV : 0;
+                    const int mB = db >= 0 ? db / SV : -1;
+                    const T* xl = x + tlo + lane * V;
+                    const T* yl = DOT ? y + tlo + lane * V : nullptr;
+
+                    auto feed_step = [&](const T (&xv)[U][V], const T (&yv)[U][V], unsigned int live) {
 #pragma unroll
-                                for (int u = 0; u < U; ++u) {
-                                    ld_vec<T, V>(x + b0 + (int64_t)(32 * V) * u, aligned, xv[u]);
-                                    if constexpr (DOT) ld_vec<T, V>(y + b0 + (int64_t)(32 * V) * u, aligned, yv[u]);
-                                }
+                        for (int u = 0; u < U; ++u)
+#pragma unroll
+                            for (int l = 0; l < V; ++l) {
+                                if (step_v<VAR> == KAHAN && !((live >> (u * V + l)) & 1u)) continue;
+                                feed<VAR, DOT>(cs[u * V + l], ce[u * V + l], xv[u][l],
+                                               DOT ? yv[u][l] : T(0), one);
+                            }
+                    };
+                    auto load_full = [&](int mb, T (&xv)[U][V], T (&yv)[U][V]) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            ld_vec<T, V>(xl + (mb + u) * SV, aligned, xv[u]);
+                            if constexpr (DOT) ld_vec<T, V>(yl + (mb + u) * SV, aligned, yv[u]);
+                        }
+                    };
+                    // a step with slots outside the piece: those elements are +0
+                    // (Kahan chains skip them)
+                    auto partial_step = [&](int mb) {
+                        T xv[U][V], yv[U][V];
+                        unsigned int live = ~0u;
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int m = mb + u;
+                            if (m >= mA && m <= mB) {
+                                ld_vec<T, V>(xl + m * SV, aligned, xv[u]);
+                                if constexpr (DOT) ld_vec<T, V>(yl + m * SV, aligned, yv[u]);
                             } else {
 #pragma unroll
-                                for (int u = 0; u < U; ++u) {
-                                    const int64_t m = mb + u;
-                                    const int64_t base = b0 + (int64_t)(32 * V) * u;
-                                    if (m >= mlo && m <= mhi && base >= pa && base + V <= pb) {
-                                        ld_vec<T, V>(x + base, aligned, xv[u]);
-                                        if constexpr (DOT) ld_vec<T, V>(y + base, aligned, yv[u]);
-                                    } else {
-#pragma unroll
-                                        for (int l = 0; l < V; ++l) {
-                                            const int64_t i = base + l;
-                                            const bool in = m >= mlo && m <= mhi && i >= pa && i < pb;
-                                            xv[u][l] = in ? x[i] : T(0);
-                                            if constexpr (DOT) yv[u][l] = in ? y[i] : T(0);
-                                            if (!in) live &= ~(1u << (u * V + l));
-                                        }
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u)
-#pragma unroll
                                 for (int l = 0; l < V; ++l) {
-                                    if (step_v<VAR> == KAHAN && !((live >> (u * V + l)) & 1u)) continue;
-                                    feed<VAR, DOT>(cs[u * V + l], ce[u * V + l], xv[u][l],
-                                                   DOT ? yv[u][l] : T(0));
+                                    const int r = m * SV + l;      // offset from xl
+                                    const int i = r + lane * V;    // tile-relative index
+                                    const bool in = m >= mlo && m <= mhi && i >= ra && i < rb;
+                                    xv[u][l] = in ? xl[r] : T(0);
+                                    if constexpr (DOT) yv[u][l] = in ? yl[r] : T(0);
+                                    if (!in) live &= ~(1u << (u * V + l));
                                 }
-                        }
-#pragma unroll
-                        for (int w = C / 2; w >= 1; w >>= 1)
-#pragma unroll
-                            for (int c = 0; c < w; ++c) merge<TW>(cs[c], ce[c], cs[c + w], ce[c + w]);
-                        A pv = cs[0], pe = ce[0];
-                        warp_fold<TW>(pv, pe);
-
-                        if (a >= tlo && b <= thi) {
-                            // the whole segment lies in this tile
-                            if (lane == 0) write_out<T, VAR, G>(out, s, (G)pv, (G)pe, out_f64 != 0);
-                        } else {
-                            const int64_t w0 = a / tile, w1 = (b - 1) / tile;
-                            const int64_t k = w1 - w0 + 1;
-                            const int64_t slot = (a < tlo) ? 2 * t : 2 * t + 1;
-                            unsigned int old = 0;
-                            if (lane == 0) {
-                                pieces[2 * slot] = (G)pv;
-                                pieces[2 * slot + 1] = (G)pe;
-                                __threadfence();
-                                old = atomicAdd(&cnt[s], 1u);
                             }
-                            old = __shfl_sync(FULL, old, 0);
-                            if ((int64_t)old == k - 1) {
-                                // last piece of the segment: merge the k pieces in tile order
-                                __threadfence();
-                                G gv = G(0), ge = G(0);
-                                if (lane < k) {
-                                    const int64_t s0 = (lane == 0) ? 2 * w0 + 1 : 2 * (w0 + lane);
-                                    ld_pair_cg(pieces + 2 * s0, gv, ge);
-                                    for (int64_t i = lane + 32; i < k; i += 32) {
-                                        G v2, e2;
-                                        ld_pair_cg(pieces + 2 * (2 * (w0 + i)), v2, e2);
-                                        merge<TW>(gv, ge, v2, e2);
+                        }
+                        feed_step(xv, yv, live);
+                    };
+
+                    // steps mb = (mlo/U)*U, ... <= mhi, in order: partial ones,
+                    // then those wholly inside the piece, then partial ones
+                    const int full0 = (mA + U - 1) / U * U;
+                    int mb = (mlo / U) * U;
+                    for (; mb < full0 && mb <= mhi; mb += U) partial_step(mb);
+                    if (mb + (U - 1) <= mB) {
+                        if constexpr (PREFETCH) {
+                            T xv[U][V], yv[U][V];
+                            load_full(mb, xv, yv);
+                            for (;;) {
+                                const int mn = mb + U;
+                                const bool more = mn + (U - 1) <= mB;
+                                T xn[U][V], yn[U][V];
+                                if (more) load_full(mn, xn, yn);
+                                feed_step(xv, yv, ~0u);
+                                mb = mn;
+                                if (!more) break;
+#pragma unroll
+                                for (int u = 0; u < U; ++u)
+#pragma unroll
+                                    for (int l = 0; l < V; ++l) {
+                                        xv[u][l] = xn[u][l];
+                                        if constexpr (DOT) yv[u][l] = yn[u][l];
                                     }
-                                }
-                                warp_fold<TW>(gv, ge);
-                                if (lane == 0) {
-                                    write_out<T, VAR, G>(out, s, gv, ge, out_f64 != 0);
-                                    cnt[s] = 0u;
-                                }
+                            }
+                        } else {
+                            for (; mb + (U - 1) <= mB; mb += U) {
+                                T xv[U][V], yv[U][V];
+                                load_full(mb, xv, yv);
+                                feed_step(xv, yv, ~0u);
                             }
                         }
                     }
-                    if (b > thi) break;                 // segment continues in the next tile
-                    if (++s >= nseg) break;
-                    a = b;
-                    b = off[s + 1];
-                    if (a >= thi) break;                // next segment starts in a later tile
+                    for (; mb <= mhi; mb += U) partial_step(mb);
+
+                    piece_finish<T, VAR, C>(cs, ce, s, a, b, (int64_t)t, tlo, thi, tile, out, cnt,
+                                            pieces, lane, out_f64);
                 }
+                if (b > thi) break;                 // segment continues in the next tile
+                if (++s >= nseg) break;
+                a = b;
+                b = __ldg(off + s + 1);
+                if (a >= thi) break;                // next segment starts in a later tile
             }
+            t = __shfl_sync(FULL, tn, 0);
         }
     }
 
-    // the last block to finish clears the per-call flag
+    // the last block to finish clears the per-call flag and the tile counter
     __syncthreads();
     __shared__ int am_last;
     if (threadIdx.x == 0) {
         __threadfence();
-        unsigned int t = atomicAdd(&hdr->ticket2, 1u);
-        am_last = (t == gridDim.x - 1);
+        unsigned int tk = atomicAdd(&hdr->ticket2, 1u);
+        am_last = (tk == gridDim.x - 1);
     }
     __syncthreads();
     if (am_last && threadIdx.x == 0) {
         hdr->call_bad = 0;
+        hdr->tile_next = 0ull;
         hdr->ticket2 = 0u;
     }
 }
@@ -225,17 +243,23 @@ static cudaError_t launch_u(int unroll, const void* x, const void* y, int64_t n,
                             int out_f64, cudaStream_t st) {
     (void)ws_bytes;
     unsigned char* w = static_cast<unsigned char*>(ws);
-    const size_t cnt_bytes = ((size_t)(nseg > 0 ? nseg : 1) * 4 + 255) / 256 * 256;
-    const int pblocks = (int)std::min<int64_t>(1024, (nseg + 1 + 255) / 256);
-    csr_prepare<T, VAR><<<pblocks, 256, 0, st>>>(off, nseg, n, out, w, out_f64);
+    const size_t cnt_bytes = csr_cnt_bytes(nseg);
+    int64_t* tile_seg = reinterpret_cast<int64_t*>(w + kHeaderBytes + cnt_bytes +
+                                                   csr_max_tiles(n) * 2 * kPairBytes);
+    const int64_t items = std::max<int64_t>(nseg + 1, (n + tile - 1) / tile);
+    const int pblocks = (int)std::min<int64_t>(1024, (items + 255) / 256);
+    csr_prepare<T, VAR><<<pblocks, 256, 0, st>>>(off, nseg, n, tile, out, w, tile_seg, out_f64);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    if (aligned && csr_tma_usable(sizeof(T) == 4 ? 0 : 1, DOT ? 1 : 0, block, tile))
+        return launch_csr_tma(sizeof(T) == 4 ? 0 : 1, VAR, DOT ? 1 : 0, unroll, x, y, off, nseg, out,
+                              w, cnt_bytes, tile_seg, block, grid, tile, out_f64, st);
     const T* xp = static_cast<const T*>(x);
     const T* yp = static_cast<const T*>(y);
     switch (unroll) {
-    case 1: csr_kernel<T, VAR, DOT, 1><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile, aligned, out_f64); break;
-    case 2: csr_kernel<T, VAR, DOT, 2><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile, aligned, out_f64); break;
-    case 4: csr_kernel<T, VAR, DOT, 4><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile, aligned, out_f64); break;
+    case 1: csr_kernel<T, VAR, DOT, 1><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile_seg, tile, aligned, out_f64); break;
+    case 2: csr_kernel<T, VAR, DOT, 2><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile_seg, tile, aligned, out_f64); break;
+    case 4: csr_kernel<T, VAR, DOT, 4><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile_seg, tile, aligned, out_f64); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -207,15 +207,30 @@ __device__ __forceinline__ double sum_error_h64(unsigned long long A, unsigned l
                                             ((mag << (52 - pr)) & M52)));
 }
 
+// A binary64 add issued as a fused multiply-add by `one` == 1.0: RN(a*1 + b)
+// = RN(a + b) for every input, signed zeros included (-0*1 + +0 = +0,
+// -0*1 + -0 = -0).  GB300 issues DFMA at 626 G/s against DADD's 528 G/s, so
+// the binary64 sums add this way; `one` must be a value the compiler cannot
+// see (a load of g_one), since a known 1.0 is folded back into a DADD.
+static __device__ double g_one = 1.0;   // never written: read once per kernel as `one`
+
+template <bool FMA>
+__device__ __forceinline__ double dadd(double a, double b, double one) {
+    if constexpr (FMA) return __fma_rn(a, one, b);
+    else return __dadd_rn(a, b);
+}
+
 // TWO-SUM(a, b): x = RN(a + b), y = a + b - x.  False (x, y untouched) unless
 // both exponent fields lie in [54, 2044]; then the caller uses two_sum.
-__device__ __forceinline__ bool two_sum_h64(double a, double b, double& x, double& y) {
+template <bool FMA = false>
+__device__ __forceinline__ bool two_sum_h64(double a, double b, double& x, double& y,
+                                            double one = 1.0) {
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
     const unsigned long long B = (unsigned long long)__double_as_longlong(b);
     const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
     const int emin = min(ea, eb);
     if (emin < 54 || max(ea, eb) > 2044) return false;
-    x = __dadd_rn(a, b);
+    x = dadd<FMA>(a, b, one);
     y = sum_error_h64(A, B, ea, eb, emin, x);
     return true;
 }
@@ -227,13 +242,15 @@ __device__ __forceinline__ bool two_sum_h64(double a, double b, double& x, doubl
 // is b moved by 0 or one ulp(b) (0, 1 or 2 half-ulps below a power of two),
 // chosen by comparing |err| with ulp/2 (ulp/4 and 3ulp/4 below a power of
 // two), ties to even.
-__device__ __forceinline__ bool fast_two_sum_h64(double a, double b, double& x, double& y) {
+template <bool FMA = false>
+__device__ __forceinline__ bool fast_two_sum_h64(double a, double b, double& x, double& y,
+                                                 double one = 1.0) {
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
     const unsigned long long B = (unsigned long long)__double_as_longlong(b);
     const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
     const int emin = min(ea, eb);
     if (emin < 54 || max(ea, eb) > 2044) return false;
-    x = __dadd_rn(a, b);
+    x = dadd<FMA>(a, b, one);
     const double err = sum_error_h64(A, B, ea, eb, emin, x);
     if (ea >= eb) { y = err; return true; }
     const unsigned long long E = (unsigned long long)__double_as_longlong(err);
@@ -513,10 +530,12 @@ template <int VAR> constexpr int step_v = VAR == FAST_LIT ? FAST : (VAR == RIG_L
 //   plain:                s = s + y
 //   wide:                 S = S + y in binary64 (binary32 products are exact
 //                         in binary64)
+// `one` is a runtime 1.0 (see dadd): binary64 sums issue their adds as DFMA.
 template <int VAR, bool DOT, typename T, typename A>
-__device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
+__device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
     constexpr int STEP = step_v<VAR>;
     constexpr bool TPROD = DOT && (VAR == FAST || VAR == RIGOROUS);   // TwoProduct error kept
+    constexpr bool FMA = sizeof(T) == 8 && !DOT;
     if constexpr (VAR == WIDE && sizeof(T) == 8) {
         // binary64 data: binary128 accumulator, products exact in binary128
         s = q_add(s, DOT ? q_mul_exact(a, b) : q128(a));
@@ -529,8 +548,12 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
         }
         s = __dadd_rn(s, p);
     } else if constexpr (VAR == PLAIN) {
-        T p = DOT ? mul_rn(a, b) : a;
-        s = add_rn(s, p);
+        if constexpr (FMA) {
+            s = dadd<true>(s, a, one);
+        } else {
+            T p = DOT ? mul_rn(a, b) : a;
+            s = add_rn(s, p);
+        }
     } else if constexpr (sizeof(T) == 8) {
         // binary64: the error-free transforms take one binary64 add (or none
         // for the product) plus integer work; the bits are those of the
@@ -548,16 +571,16 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b) {
         }
         double t, y;
         if constexpr (STEP == KAHAN) {
-            const double yk = add_rn(p, e);
-            if (!fast_two_sum_h64(s, yk, t, y)) { const double2 r = fast_two_sum_slow(s, yk); t = r.x; y = r.y; }
+            const double yk = dadd<FMA>(p, e, one);
+            if (!fast_two_sum_h64<FMA>(s, yk, t, y, one)) { const double2 r = fast_two_sum_slow(s, yk); t = r.x; y = r.y; }
             e = y;
         } else {
             if constexpr (STEP == FAST) {
-                if (!fast_two_sum_h64(s, p, t, y)) { const double2 r = fast_two_sum_slow(s, p); t = r.x; y = r.y; }
+                if (!fast_two_sum_h64<FMA>(s, p, t, y, one)) { const double2 r = fast_two_sum_slow(s, p); t = r.x; y = r.y; }
             } else {
-                if (!two_sum_h64(s, p, t, y)) { const double2 r = two_sum_slow(s, p); t = r.x; y = r.y; }
+                if (!two_sum_h64<FMA>(s, p, t, y, one)) { const double2 r = two_sum_slow(s, p); t = r.x; y = r.y; }
             }
-            if constexpr (TPROD) e = add_rn(e, add_rn(y, ep)); else e = add_rn(e, y);
+            if constexpr (TPROD) e = add_rn(e, add_rn(y, ep)); else e = dadd<FMA>(e, y, one);
         }
         s = t;
     } else {
@@ -683,6 +706,7 @@ struct WsHeader {
     int call_bad;            // batched: offsets of the current call are invalid
     unsigned int ticket2;    // batched: blocks done (reset by the last)
     double stage[2];         // host-buffer calls: the output pair
+    unsigned long long tile_next;   // batched: next tile to claim (reset by the last block)
 };
 constexpr size_t kWsHeader = 256;
 

@@ -26,6 +26,8 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
     A s[C], e[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) { s[c] = A(0); e[c] = A(0); }
+    double one = 1.0;                 // binary64 sums: a 1.0 the compiler cannot see
+    if constexpr (sizeof(T) == 8 && !DOT) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const int64_t nv = n / V;
     const int tail = (int)(n - nv * V);
@@ -44,7 +46,7 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int l = 0; l < V; ++l)
-                feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[u][l], DOT ? yv[u][l] : T(0));
+                feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[u][l], DOT ? yv[u][l] : T(0), one);
     }
     // fewer than U full vectors left for this thread, and maybe the partial
     // vector n/V (owned by the thread with g = (n/V) mod P)
@@ -57,14 +59,14 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
             if constexpr (DOT) ld_vec<T, V>(y + jj * V, aligned, yv);
 #pragma unroll
             for (int l = 0; l < V; ++l)
-                feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[l], DOT ? yv[l] : T(0));
+                feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[l], DOT ? yv[l] : T(0), one);
         } else if (jj == nv && tail > 0) {
 #pragma unroll
             for (int l = 0; l < V; ++l)
                 if (l < tail) {
                     T a = x[jj * V + l];
                     T b = DOT ? y[jj * V + l] : T(0);
-                    feed<VAR, DOT>(s[u * V + l], e[u * V + l], a, b);
+                    feed<VAR, DOT>(s[u * V + l], e[u * V + l], a, b, one);
                 }
         }
     }

@@ -24,6 +24,14 @@ cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* 
                        void* out, void* ws, size_t ws_bytes, int block, int64_t grid,
                        int64_t tile, int aligned, int out_f64, cudaStream_t st);
 size_t csr_ws_bytes(int64_t n, int64_t nseg);
+// the batched kernel staged through shared memory by bulk copies (16-byte
+// aligned inputs; plans whose tile and block fit its ring)
+bool csr_tma_usable(int dtype, int dot, int block, int64_t tile);
+size_t csr_tma_smem_bytes(int dot, int block);
+cudaError_t launch_csr_tma(int dtype, int variant, int dot, int unroll, const void* x,
+                           const void* y, const int64_t* off, int64_t nseg, void* out,
+                           unsigned char* ws, size_t cnt_bytes, const int64_t* tile_seg,
+                           int block, int64_t grid, int64_t tile, int out_f64, cudaStream_t st);
 
 cudaError_t launch_prim(int prim, int dtype, const void* a, const void* b, void* x, void* y,
                         int64_t n, cudaStream_t st);

@@ -105,6 +105,17 @@ def signed_lognormal(n, dtype="f32", sigma=2.0, seed=0, stream=0, device="cpu") 
     return (sign * torch.exp(sigma * z)).to(td)
 
 
+def ternary_i8(n, seed=0, stream=0, device="cpu") -> torch.Tensor:
+    """Values in {-1, 0, +1} (int8), from the word's bits 40..63 mod 3; built a
+    chunk at a time so that n may exceed 2^31."""
+    out = torch.empty(n, dtype=torch.int8, device=device)
+    for lo in range(0, n, _CHUNK):
+        hi = min(n, lo + _CHUNK)
+        w = words(hi - lo, seed, stream, device, start=lo)
+        out[lo:hi] = (_srl(w, 40) % 3 - 1).to(torch.int8)
+    return out
+
+
 def csr_lengths(nseg, lmin=16, lmax=1 << 18, seed=0, stream=0) -> np.ndarray:
     """Segment lengths floor(exp(U(ln lmin, ln lmax))) (log-uniform), host int64."""
     w = words(nseg, seed, stream, "cpu")

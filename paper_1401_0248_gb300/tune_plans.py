@@ -33,6 +33,9 @@ def main(argv=None):
     ap.add_argument("--nseg", type=int, default=16384)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--flat-only", action="store_true")
+    ap.add_argument("--batched-only", action="store_true")
+    ap.add_argument("--variants", default="plain,fast,rigorous,wide,kahan",
+                    help="comma list of plain, fast, rigorous, wide, kahan")
     ap.add_argument("--dtypes", default="f32,f64", help="comma list of f32, f64")
     ap.add_argument("--load", default=None, help="start from this plan file")
     args = ap.parse_args(argv)
@@ -45,27 +48,25 @@ def main(argv=None):
     if args.load:
         tf.plan_load(args.load)
     t0 = time.time()
+    variants = args.variants.split(",")
     for dt, td in (("f32", torch.float32), ("f64", torch.float64)):
         if dt not in args.dtypes.split(","):
             continue
-        n = args.n
-        x = I.uniform(n, dt, seed=0, device=dev)
-        y = I.uniform(n, dt, seed=0, stream=1, device=dev)
-        for op in ("sum", "dot"):
-            for variant in ("plain", "fast", "rigorous", "wide", "kahan"):
-                if variant == "wide" and dt == "f64":
-                    continue
-                p = tf.tune(op, variant, x, y if op == "dot" else None, reps=args.reps)
-                print("flat    %s %s %-8s -> %s" % (dt, op, variant, p), flush=True)
-        del x, y
+        if not args.batched_only:
+            n = args.n
+            x = I.uniform(n, dt, seed=0, device=dev)
+            y = I.uniform(n, dt, seed=0, stream=1, device=dev)
+            for op in ("sum", "dot"):
+                for variant in variants:
+                    p = tf.tune(op, variant, x, y if op == "dot" else None, reps=args.reps)
+                    print("flat    %s %s %-8s -> %s" % (dt, op, variant, p), flush=True)
+            del x, y
         if args.flat_only:
             continue
         xs = I.uniform(total, dt, seed=1, device=dev)
         ys = I.uniform(total, dt, seed=1, stream=1, device=dev)
         for op in ("sum", "dot"):
-            for variant in ("plain", "fast", "rigorous", "wide", "kahan"):
-                if variant == "wide" and dt == "f64":
-                    continue
+            for variant in variants:
                 p = tf.tune(op, variant, xs, ys if op == "dot" else None, offsets=off,
                             reps=args.reps)
                 print("batched %s %s %-8s -> %s" % (dt, op, variant, p), flush=True)

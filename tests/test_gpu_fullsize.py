@@ -15,6 +15,10 @@ C4  16,384 ragged binary32 segments (log-uniform 16 .. 2^18 elements, ~4.4e8
 C5  binary64 twofold dot, N = 2^29, cond 1e8 .. 1e30: rigorous within the
     bound of the known exact dot, the error term tracking value - exact, and
     20 runs bit-identical.
+C6  the largest sizes: N = 2^31 + 1234567 elements (past 32-bit indexing),
+    flat and batched (segments straddling element 2^31), binary32 and
+    binary64, on data in {-1, 0, +1} whose partial sums stay far below 2^24,
+    so every order gives the exact integer sum and error +0.
 """
 import math
 import os
@@ -205,4 +209,35 @@ def test_c5_f64_dot_n2p29_cond_sweep_tracking_and_reproducible():
                 assert same_bits(run("dot", "rigorous", ic.x, ic.y), rig)
                 assert same_bits(run("dot", "fast", ic.x, ic.y), fast)
         del ic
+        torch.cuda.empty_cache()
+
+
+def test_c6_beyond_2p31_elements_exact_integer_sums():
+    n = (1 << 31) + 1234567
+    x8 = I.ternary_i8(n, seed=3, stream=0, device=DEV)
+    y8 = I.ternary_i8(n, seed=3, stream=1, device=DEV)
+    hx, hy = _np(x8), _np(y8)
+    off_h = np.array([0, (1 << 30) + 3, (1 << 31) - 5, (1 << 31) + 77, n, n], dtype=np.int64)
+    nseg = off_h.size - 1
+    S = [int(np.sum(hx[off_h[k]:off_h[k + 1]], dtype=np.int64)) for k in range(nseg)]
+    D = [0] * nseg
+    for k in range(nseg):
+        for a in range(off_h[k], off_h[k + 1], 1 << 26):
+            b = min(off_h[k + 1], a + (1 << 26))
+            D[k] += int(np.sum(hx[a:b].astype(np.int16) * hy[a:b], dtype=np.int64))
+    assert max(abs(v) for v in S + D) < 1 << 20
+    off = torch.from_numpy(off_h).to(DEV)
+    for dt in ("f32", "f64"):
+        x, y = x8.to(TD[dt]), y8.to(TD[dt])
+        for variant in ("fast", "rigorous", "plain"):
+            got = run("sum", variant, x)
+            assert got[0] == sum(S) and got[1] == 0, (dt, variant, got, sum(S))
+        got = run("dot", "rigorous", x, y)
+        assert got[0] == sum(D) and got[1] == 0, (dt, got, sum(D))
+        for op, want in (("sum", S), ("dot", D)):
+            out = _np(tf.sum_batched(x, off, "rigorous") if op == "sum"
+                      else tf.dot_batched(x, y, off, "rigorous"))
+            assert [float(v) for v in out[:, 0]] == [float(v) for v in want], (dt, op)
+            assert not out[:, 1].any()
+        del x, y
         torch.cuda.empty_cache()
