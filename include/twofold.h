@@ -247,6 +247,16 @@ tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink
 tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
                        tf_stream_t stream);
 
+/* The bounded wait of the batched kernel's shared-memory ring (an mbarrier
+   phase polled at most `polls` times, 1 <= polls <= 2^22), run by one thread
+   on a barrier that nothing completes (arrive = 0) or that the thread
+   completes first (arrive = 1).  Writes *flag (device int32) = 1 if the wait
+   gave up, else 0.  This is how the kernels' waits end without a result: the
+   batched kernel then sets TF_ERR_TIMEOUT in the workspace error word
+   (tf_get_device_error) and returns.  Argument errors come back before any
+   launch. */
+tf_status tf_probe_wait(int32_t arrive, int64_t polls, int32_t* flag, tf_stream_t stream);
+
 /* ---- misc -------------------------------------------------------------- */
 const char* tf_status_string(tf_status s);
 /* SM count of the current device (0 if none). */

@@ -462,4 +462,14 @@ tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int3
                    cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
 
+tf_status tf_probe_wait(int32_t arrive, int64_t polls, int32_t* flag, tf_stream_t stream) {
+    if ((arrive != 0 && arrive != 1) || polls < 1 || polls > (1 << 22) || !flag) return TF_ERR_ARG;
+    if ((uintptr_t)flag % 4) return TF_ERR_ALIGN;
+    int sms = 0;
+    tf_status s = check_device(&sms);
+    if (s != TF_OK) return s;
+    return tf::launch_probe_wait(arrive, polls, flag, (cudaStream_t)stream) == cudaSuccess
+               ? TF_OK : TF_ERR_CUDA;
+}
+
 }  // extern "C"

@@ -7,6 +7,7 @@
 //                 reductions' 128-bit loads and no arithmetic.
 //   alu_probe     the paper's p-functions: the per-item operations from
 //                 registers, 8 independent chains per thread, no loads.
+#include "tf_async.cuh"
 #include "tf_device.cuh"
 #include "tf_internal.h"
 
@@ -262,6 +263,25 @@ cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, in
     case 13: alu_probe<13><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// The batched kernel's bounded mbarrier wait, on one barrier of one thread:
+// with arrive = 0 nothing completes the phase and the wait gives up after
+// `polls` polls; with arrive = 1 the thread completes it first.  flag[0] = 1
+// if the wait gave up, else 0; the barrier is then released, nothing is left
+// in flight and the context stays usable.
+__global__ void wait_probe_kernel(int arrive, unsigned polls, int* flag) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (arrive) mbar_arrive_expect_tx(b, 0);
+    flag[0] = mbar_wait(b, 0, polls) ? 0 : 1;
+}
+
+cudaError_t launch_probe_wait(int arrive, int64_t polls, int* flag, cudaStream_t st) {
+    wait_probe_kernel<<<1, 1, 0, st>>>(arrive, (unsigned)polls, flag);
     return cudaGetLastError();
 }
 

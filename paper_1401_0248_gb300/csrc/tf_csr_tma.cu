@@ -18,6 +18,7 @@
 // a wait that gives up sets TF_ERR_TIMEOUT in the workspace's error word,
 // waits (bounded again) for the warp's copies in flight and ends the warp's
 // work.
+#include "tf_async.cuh"
 #include "tf_csr.cuh"
 
 #include <atomic>
@@ -26,56 +27,14 @@ namespace tf {
 
 namespace {
 
-constexpr int kRows = 4;                       // slot rows per chunk
+constexpr int kRows = 8;                       // slot rows per chunk
 constexpr int kRowBytes = 32 * 16;             // one row: 32 lanes x 16 bytes
-constexpr int kChunkBytes = kRows * kRowBytes;  // 2 KiB per operand
-constexpr int kStages = 4;
+constexpr int kChunkBytes = kRows * kRowBytes;  // 4 KiB per operand
+constexpr int kStages = 3;
 constexpr int kMaxWarps = 16;
 constexpr int kTfErrTimeout = 7;               // TF_ERR_TIMEOUT
 constexpr unsigned kWaitLimit = 1u << 20;      // try_wait rounds before giving up
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (unsigned i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void ld_shared(uint32_t a, float (&r)[4]) {
-    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3])
-                 : "r"(a));
-}
-__device__ __forceinline__ void ld_shared(uint32_t a, double (&r)[2]) {
-    asm volatile("ld.shared.v2.f64 {%0,%1}, [%2];" : "=d"(r[0]), "=d"(r[1]) : "r"(a));
-}
 
 }  // namespace
 
@@ -133,20 +92,21 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
         t = __shfl_sync(FULL, t, 0);
         if (lane == 0) tn_raw = atomicAdd(&hdr->tile_next, 1ull);
         int64_t tn = -1;                          // the next tile, once read
-        int64_t pt = (int64_t)t, pc = 0;
+        int64_t pt = (int64_t)t, pc = 0, pnc = (int64_t)t < ntiles ? nchunks((int64_t)t) : 0;
         uint32_t issued = 0, freed = 0, kbase = 0;
         bool failed = false;
 
         // lane 0 issues chunks while the ring has room: the rest of tile t,
         // then the next claimed tile (read from the claim only when needed)
         auto top_up = [&]() {
-            while (issued < freed + kStages && pt < ntiles) {
-                if (pc >= nchunks(pt)) {
+            while (issued < freed + kStages) {
+                if (pc >= pnc) {
                     if (pt != (int64_t)t) break;            // one tile ahead at most
                     if (tn < 0) tn = (int64_t)__shfl_sync(FULL, tn_raw, 0);
+                    if (tn >= ntiles) break;
                     pt = tn;
                     pc = 0;
-                    continue;
+                    pnc = nchunks(pt);
                 }
                 if (lane == 0) {
                     const int64_t e0 = pt * tile + pc * CE;
@@ -169,56 +129,67 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
         while (!failed && (int64_t)t < ntiles) {
             const int64_t tlo = (int64_t)t * tile;
             const int64_t thi = min(tlo + tile, total);
+            // tile-relative end of the bulk-copied data (elements past it are
+            // read from global memory)
+            const int vrel = (int)max((int64_t)0, min(vend - tlo, tile));
             top_up();
             int64_t s = __ldg(tile_seg + t);
             int64_t a = __ldg(off + s), b = __ldg(off + s + 1);
             int cur = -1;                          // chunk of the tile being read
+
+            // chunks before ch are read: free them, refill the ring, wait for ch
+            auto ensure = [&](int ch) {
+                if (ch == cur) return;
+                __syncwarp();
+                freed = kbase + (uint32_t)ch;
+                top_up();
+                const uint32_t k = kbase + (uint32_t)ch;
+                const bool ok = mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u, kWaitLimit);
+                failed = __any_sync(FULL, !ok);
+                cur = ch;
+            };
+            auto row_addr = [&](int row) {
+                return ring + ((kbase + (uint32_t)(row / kRows)) % kStages) * kStageBytes +
+                       (uint32_t)(((row % kRows) * 32 + lane) * 16);
+            };
+
             for (;;) {
                 const int64_t pa = max(a, tlo), pb = min(b, thi);
                 if (pb > pa) {
                     A cs[C], ce[C];
 #pragma unroll
                     for (int c = 0; c < C; ++c) { cs[c] = A(0); ce[c] = A(0); }
-                    const int m0 = (int)((pa - tlo) / SV), m1 = (int)((pb - 1 - tlo) / SV);
-                    for (int mb = (m0 / U) * U; mb <= m1 && !failed; mb += U) {
-                        const int ch = mb / kRows;
-                        if (ch != cur) {
-                            // chunks before ch are read: free them, refill, wait for ch
-                            __syncwarp();
-                            freed = kbase + (uint32_t)ch;
-                            top_up();
-                            const uint32_t k = kbase + (uint32_t)ch;
-                            if (!mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u)) failed = true;
-                            failed = __any_sync(FULL, failed);
-                            if (failed) break;
-                            cur = ch;
-                        }
-                        const uint32_t sbase = ring + ((kbase + (uint32_t)ch) % kStages) * kStageBytes;
-                        const int64_t r0 = tlo + (int64_t)mb * SV;            // first element of the step
-                        const bool full = r0 >= pa && r0 + U * SV <= pb && r0 + U * SV <= vend;
+                    // tile-relative piece [ra, rb); rows m0..m1 touch it; steps
+                    // mb in [fs, fe] lie wholly inside [ra, min(rb, vrel))
+                    const int ra = (int)(pa - tlo), rb = (int)(pb - tlo);
+                    const int rbv = min(rb, vrel);
+                    const int m0 = ra / SV, m1 = (rb - 1) / SV;
+                    const int fs = ((ra + SV - 1) / SV + U - 1) / U * U;
+                    const int fe = rbv / SV - U;
+
+                    // a step with elements outside the piece (+0; Kahan skips
+                    // them) or past the bulk copies (read from global memory)
+                    auto step_masked = [&](int mb) {
                         T xv[U][V], yv[U][V];
                         unsigned int live = ~0u;
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             const int row = mb + u;
-                            const uint32_t sa = sbase + (uint32_t)(((row % kRows) * 32 + lane) * 16);
+                            const uint32_t sa = row_addr(row);
                             ld_shared(sa, xv[u]);
                             if constexpr (DOT) ld_shared(sa + kChunkBytes, yv[u]);
-                            if (!full) {
-                                const int64_t v0 = tlo + (int64_t)row * SV + (int64_t)lane * V;
 #pragma unroll
-                                for (int l = 0; l < V; ++l) {
-                                    const int64_t i = v0 + l;
-                                    const bool in = i >= pa && i < pb;
-                                    if (in && i >= vend) {           // past the bulk copies
-                                        xv[u][l] = x[i];
-                                        if constexpr (DOT) yv[u][l] = y[i];
-                                    }
-                                    if (!in) {
-                                        xv[u][l] = T(0);
-                                        if constexpr (DOT) yv[u][l] = T(0);
-                                        live &= ~(1u << (u * V + l));
-                                    }
+                            for (int l = 0; l < V; ++l) {
+                                const int i = row * SV + lane * V + l;
+                                const bool in = i >= ra && i < rb;
+                                if (in && i >= vrel) {
+                                    xv[u][l] = x[tlo + i];
+                                    if constexpr (DOT) yv[u][l] = y[tlo + i];
+                                }
+                                if (!in) {
+                                    xv[u][l] = T(0);
+                                    if constexpr (DOT) yv[u][l] = T(0);
+                                    live &= ~(1u << (u * V + l));
                                 }
                             }
                         }
@@ -230,6 +201,40 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
                                 feed<VAR, DOT>(cs[u * V + l], ce[u * V + l], xv[u][l],
                                                DOT ? yv[u][l] : T(0), one);
                             }
+                    };
+
+                    int mb = (m0 / U) * U;
+                    for (; !failed && mb <= m1 && mb < fs; mb += U) {
+                        ensure(mb / kRows);
+                        if (!failed) step_masked(mb);
+                    }
+                    // whole steps, a chunk at a time
+                    while (!failed && mb <= fe) {
+                        const int ch = mb / kRows;
+                        ensure(ch);
+                        if (failed) break;
+                        const uint32_t cb = ring + ((kbase + (uint32_t)ch) % kStages) * kStageBytes +
+                                            (uint32_t)(lane * 16);
+                        const int mend = min(fe, (ch + 1) * kRows - U);
+                        for (; mb <= mend; mb += U) {
+                            T xv[U][V], yv[U][V];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const uint32_t sa = cb + (uint32_t)(((mb + u) % kRows) * kRowBytes);
+                                ld_shared(sa, xv[u]);
+                                if constexpr (DOT) ld_shared(sa + kChunkBytes, yv[u]);
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+#pragma unroll
+                                for (int l = 0; l < V; ++l)
+                                    feed<VAR, DOT>(cs[u * V + l], ce[u * V + l], xv[u][l],
+                                                   DOT ? yv[u][l] : T(0), one);
+                        }
+                    }
+                    for (; !failed && mb <= m1; mb += U) {
+                        ensure(mb / kRows);
+                        if (!failed) step_masked(mb);
                     }
                     if (failed) break;
                     piece_finish<T, VAR, C>(cs, ce, s, a, b, (int64_t)t, tlo, thi, tile, out, cnt,
@@ -250,12 +255,16 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
             t = (unsigned long long)tn;
             tn = -1;
             if ((int64_t)t < ntiles && lane == 0) tn_raw = atomicAdd(&hdr->tile_next, 1ull);
-            if (pt != (int64_t)t) { pt = (int64_t)t; pc = 0; }   // nothing issued for it yet
+            if (pt != (int64_t)t) {                          // nothing issued for it yet
+                pt = (int64_t)t;
+                pc = 0;
+                pnc = (int64_t)t < ntiles ? nchunks((int64_t)t) : 0;
+            }
         }
         if (failed) {
             if (lane == 0) atomicExch(&hdr->error, kTfErrTimeout);
             // let the copies still in flight land before the block can exit
-            for (uint32_t k = freed; k < issued; ++k) mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u);
+            for (uint32_t k = freed; k < issued; ++k) mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u, kWaitLimit);
         }
     }
 

@@ -41,5 +41,6 @@ cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void
                               int blocks, int threads, cudaStream_t st);
 cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, int threads,
                              cudaStream_t st);
+cudaError_t launch_probe_wait(int arrive, int64_t polls, int* flag, cudaStream_t st);
 
 }  // namespace tf

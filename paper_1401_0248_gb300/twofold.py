@@ -55,6 +55,7 @@ SIGNATURES = {
     "tf_count_large_errors": ([_P, _I64, C.c_int, C.c_double, _P, _P], C.c_int),
     "tf_probe_read": ([_P, _P, _I64, _P, _I32, _I32, _P], C.c_int),
     "tf_probe_alu": ([C.c_int, _I64, _P, _I32, _I32, _P], C.c_int),
+    "tf_probe_wait": ([_I32, _I64, _P, _P], C.c_int),
     "tf_status_string": ([C.c_int], C.c_char_p),
     "tf_device_sm_count": ([], _I32),
 }
@@ -376,6 +377,16 @@ def probe_alu(kind, iters, blocks, threads, sink=None, device=None):
     _check("tf_probe_alu", lib().tf_probe_alu(k, int(iters), _ptr(sink), blocks, threads,
                                               _stream(sink)))
     return sink
+
+
+def probe_wait(arrive, polls, device=None):
+    """Run the batched kernel's bounded barrier wait on a barrier that is
+    never completed (arrive=False) or completed first (arrive=True); returns
+    True if the wait gave up."""
+    flag = torch.full((1,), -1, dtype=torch.int32, device=device or "cuda")
+    _check("tf_probe_wait", lib().tf_probe_wait(1 if arrive else 0, int(polls), _ptr(flag),
+                                                _stream(flag)))
+    return bool(int(flag.item()) == 1)
 
 
 def sm_count():

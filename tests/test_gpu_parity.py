@@ -454,6 +454,31 @@ def test_csr_tiles_and_long_segments(tile):
                             before["blocks_per_sm"], before["tile"])
 
 
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("unroll,block", [(1, 128), (2, 512), (4, 256)])
+def test_csr_staged_ring_edges(dt, unroll, block):
+    """The shared-memory ring of the batched kernel (16-byte-aligned inputs,
+    tile 4096): totals that end inside a 16-byte vector (the tail is read from
+    global memory), totals below one vector, empty segments, pieces that start
+    and end inside a chunk, and runs of tiles past the ring's depth."""
+    tile = 4096
+    cases = [[1], [3], [0, 5, 0], [tile * 3 + 3], [2, tile - 1, 7, tile * 2 + 1, 0, 9],
+             [tile * 9 + 1, 1, 1], [17] * 700]
+    for k, L in enumerate(cases):
+        off_h = I.csr_offsets(L)
+        n = int(off_h[-1])
+        x = I.uniform(max(n, 1), dt, seed=40 + k, device=DEV)[:n]
+        y = I.uniform(max(n, 1), dt, seed=40 + k, stream=3, device=DEV)[:n]
+        for op, variant in (("sum", "rigorous"), ("dot", "fast"), ("sum", "kahan")):
+            before = tf.plan_get(op, True, TD[dt], variant)
+            try:
+                tf.plan_set(op, True, TD[dt], variant, block, unroll, 2, tile)
+                check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
+            finally:
+                tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
+                            before["blocks_per_sm"], before["tile"])
+
+
 def test_csr_invalid_offsets_flagged_then_recovers():
     x = I.uniform(1000, "f32", seed=1, device=DEV)
     ws = tf.workspace(tf.workspace_size("sum", True, torch.float32, "fast", 1000, 4), DEV)
@@ -552,3 +577,16 @@ def test_probes_run():
     for k in tf.ALU_KINDS:
         tf.probe_alu(k, 100, 152, 256, device=DEV)
     torch.cuda.synchronize()
+
+
+def test_bounded_barrier_wait_gives_up_and_context_survives():
+    """The batched kernel's mbarrier wait on a barrier nothing completes ends
+    after its poll limit with a status the host reads; a completed barrier
+    passes at once; the context stays usable afterwards."""
+    assert tf.probe_wait(False, 2000, device=DEV) is True
+    assert tf.probe_wait(True, 2000, device=DEV) is False
+    x = I.normal(4099, "f32", seed=9, device=DEV)
+    got = _np(tf.sum(x, "rigorous"))
+    block, unroll, grid, _ = tf.launch_shape("sum", False, torch.float32, "rigorous", 4099)
+    want = O.replay_flat("sum", "rigorous", _np(x), block=block, unroll=unroll, grid=grid)
+    assert same_bits(got, want)
