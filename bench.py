@@ -334,7 +334,8 @@ def run_gpu(args, rank, world, local):
         name = "%s_%s_%s_c%g" % (dt, op, v, cond)
         kernels[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
                          "frac_read": round(gbs / read_bw, 4) if read_bw else None,
-                         "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
+                         "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4),
+                         "gelem_s": round(n / (ms * 1e-3) / 1e9, 2)}
         _, _, S, cond_got = data[(dt, cond)][op]
         o = outs[k].cpu().tolist()
         acc = {"cond": float("%.3g" % cond_got), "rel_err_v_plus_e": rel_err(S, o[0], o[1]),
@@ -342,6 +343,14 @@ def run_gpu(args, rank, world, local):
         if v in TWOFOLD:
             rv = S - Fraction(float(o[0]))
             acc["e_over_residual"] = (float(Fraction(float(o[1])) / rv) if rv != 0 else None)
+            # the paper's bound with gamma_{N-1} (finite for binary64 at this N):
+            # |S - (v + e)| <= u|S| + gamma_{N-1}^2 sum|x|, sum|x| = cond |S|
+            u = 2.0 ** -53 if dt == "f64" else 2.0 ** -24
+            if (n - 1) * u < 1 and S != 0:
+                g = (n - 1) * u / (1 - (n - 1) * u)
+                bound = u * abs(float(S)) + g * g * cond_got * abs(float(S))
+                err = abs(S - Fraction(float(o[0])) - Fraction(float(o[1])))
+                acc["within_literal_bound"] = bool(float(err) <= bound)
         accuracy[name] = acc
 
     # how well e estimates the value's own error: rho = e / (S - v) over the

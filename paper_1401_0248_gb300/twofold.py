@@ -20,6 +20,7 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtwofold.so")
+DEFAULT_PLANS = os.path.join(_HERE, "plans_gb300.txt")
 
 DTYPES = {torch.float32: 0, torch.float64: 1}
 VARIANTS = {"plain": 0, "fast": 1, "rigorous": 2, "wide": 3, "kahan": 4}
@@ -92,6 +93,13 @@ def lib():
                     f = getattr(L, name)
                     f.argtypes = args
                     f.restype = res
+                # the launch plans tuned on GB300 (TF_PLANS=<file> picks another
+                # file, TF_PLANS=none keeps the library's built-in defaults)
+                plans = os.environ.get("TF_PLANS", DEFAULT_PLANS)
+                if plans != "none" and os.path.exists(plans):
+                    rc = L.tf_plan_load(os.fsencode(plans))
+                    if rc != 0:
+                        raise TwofoldError("tf_plan_load(%s): %s" % (plans, STATUS.get(rc, rc)))
                 _lib = L
     return _lib
 
