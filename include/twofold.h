@@ -185,23 +185,35 @@ tf_status tf_get_device_error(void* ws, size_t ws_bytes, int32_t* code, tf_strea
 
 /* ---- plans and tuning -------------------------------------------------- */
 
+/* Plans are kept per key (op, class, dtype, variant); the class is
+   TF_PLAN_FLAT for single vectors of more than TF_SMALL_N elements,
+   TF_PLAN_BATCHED for the batched calls and TF_PLAN_FLAT_SMALL for single
+   vectors of at most TF_SMALL_N elements, whose time is set by the latency of
+   the folds rather than by memory (they want fewer, wider-spread threads).
+   The `batched` argument below takes the class. */
+#define TF_PLAN_FLAT 0
+#define TF_PLAN_BATCHED 1
+#define TF_PLAN_FLAT_SMALL 2
+#define TF_SMALL_N (1 << 22)
 tf_status tf_plan_get(tf_op op, int batched, tf_dtype dtype, tf_variant variant, tf_plan* plan);
 tf_status tf_plan_set(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
                       const tf_plan* plan);
-/* The launch shape a call of size n (or total elements n) would use. */
+/* The launch shape a call of size n (or total elements n) would use
+   (batched: 0 single vector, the class then follows from n; 1 batched). */
 tf_status tf_launch_shape(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
                           int64_t n, int32_t* block, int32_t* unroll, int64_t* grid,
                           int64_t* tile);
 /* Time every candidate plan on the given problem (device data as for the
    calls above, y/offsets NULL where unused), `reps` timed launches each after
-   two warm-up launches, keep the fastest as the plan for its key and return
-   it.  Synchronous; not capturable. */
+   two warm-up launches, keep the fastest as the plan for its key (single
+   vectors: the class of n) and return it.  Synchronous; not capturable. */
 tf_status tf_tune(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
                   const void* x, const void* y, int64_t n, const int64_t* offsets,
                   int64_t nseg, void* out, void* ws, size_t ws_bytes, int reps,
                   tf_stream_t stream, tf_plan* best);
-/* Plans as text, one line per key: "op batched dtype variant block unroll
-   blocks_per_sm tile".  Save writes a temporary file and renames it. */
+/* Plans as text, one line per key: "op class dtype variant block unroll
+   blocks_per_sm tile".  Save writes a temporary file and renames it; load
+   accepts any subset of the keys. */
 tf_status tf_plan_save(const char* path);
 tf_status tf_plan_load(const char* path);
 

@@ -24,27 +24,38 @@ struct DevInfo { int sms = 0; int ok = -1; };
 DevInfo g_dev[64];
 
 constexpr int kVariants = 5;          // plain, fast, rigorous, wide, kahan
+constexpr int kClasses = 3;           // TF_PLAN_FLAT, TF_PLAN_BATCHED, TF_PLAN_FLAT_SMALL
 
-// plans indexed [op][batched][dtype][variant]
-tf_plan g_plan[2][2][2][kVariants];
+// plans indexed [op][class][dtype][variant]
+tf_plan g_plan[2][kClasses][2][kVariants];
 bool g_plan_init = false;
 
 void init_plans_locked() {
     if (g_plan_init) return;
     for (int op = 0; op < 2; ++op)
-        for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < kClasses; ++c)
             for (int dt = 0; dt < 2; ++dt)
                 for (int v = 0; v < kVariants; ++v) {
                     tf_plan p;
                     p.block = 512;
-                    p.unroll = dt == 0 ? 2 : 2;
+                    p.unroll = 2;
                     p.blocks_per_sm = 2;
-                    p.tile = b ? (dt == 0 ? 4096 : 2048) : 0;
-                    if (b) { p.block = 256; p.blocks_per_sm = 4; }
-                    g_plan[op][b][dt][v] = p;
+                    p.tile = 0;
+                    if (c == TF_PLAN_BATCHED) {
+                        p.block = 256;
+                        p.blocks_per_sm = 4;
+                        p.tile = dt == 0 ? 4096 : 2048;
+                    } else if (c == TF_PLAN_FLAT_SMALL) {
+                        p.block = 256;
+                        p.unroll = 1;
+                    }
+                    g_plan[op][c][dt][v] = p;
                 }
     g_plan_init = true;
 }
+
+// the plan class of a single-vector call of n elements
+int flat_class(int64_t n) { return n <= (int64_t)TF_SMALL_N ? TF_PLAN_FLAT_SMALL : TF_PLAN_FLAT; }
 
 tf_status check_device(int* sms) {
     int dev = 0;
@@ -67,7 +78,8 @@ tf_status check_device(int* sms) {
     return TF_OK;
 }
 
-bool plan_valid(const tf_plan& p, int batched, int dtype) {
+bool plan_valid(const tf_plan& p, int cls, int dtype) {
+    const bool batched = cls == TF_PLAN_BATCHED;
     if (p.block != 128 && p.block != 256 && p.block != 512) return false;
     if (p.unroll != 1 && p.unroll != 2 && p.unroll != 4) return false;
     if (p.blocks_per_sm < 1 || p.blocks_per_sm > 8) return false;
@@ -132,7 +144,7 @@ tf_status run_flat(int op, const void* x, const void* y, int64_t n, int dtype, i
     if (ws_bytes < flat_ws_bytes()) return TF_ERR_WORKSPACE;
     int sms = 0;
     if ((s = check_device(&sms)) != TF_OK) return s;
-    const tf_plan p = force ? *force : get_plan(op, 0, dtype, variant);
+    const tf_plan p = force ? *force : get_plan(op, flat_class(n), dtype, variant);
     const int64_t grid = flat_grid(p, n, dtype, sms);
     const int aligned = ((uintptr_t)x % 16 == 0) && (op == 0 || (uintptr_t)y % 16 == 0);
     cudaError_t e = tf::launch_flat(dtype, kernel_variant(op, variant, flags), op, p.unroll, x, y,
@@ -276,22 +288,24 @@ tf_status tf_get_device_error(void* ws, size_t ws_bytes, int32_t* code, tf_strea
 }
 
 tf_status tf_plan_get(tf_op op, int batched, tf_dtype dtype, tf_variant variant, tf_plan* plan) {
-    if (!plan || op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1))
+    if (!plan || op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1) ||
+        batched < 0 || batched >= kClasses)
         return TF_ERR_ARG;
-    *plan = get_plan(op, batched ? 1 : 0, dtype, variant);
+    *plan = get_plan(op, batched, dtype, variant);
     return TF_OK;
 }
 
 tf_status tf_plan_set(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
                       const tf_plan* plan) {
-    if (!plan || op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1))
+    if (!plan || op < 0 || op > 1 || variant < 0 || variant >= kVariants || (dtype != 0 && dtype != 1) ||
+        batched < 0 || batched >= kClasses)
         return TF_ERR_ARG;
     tf_plan p = *plan;
-    if (!batched) p.tile = 0;
-    if (!plan_valid(p, batched ? 1 : 0, dtype)) return TF_ERR_ARG;
+    if (batched != TF_PLAN_BATCHED) p.tile = 0;
+    if (!plan_valid(p, batched, dtype)) return TF_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     init_plans_locked();
-    g_plan[op][batched ? 1 : 0][dtype][variant] = p;
+    g_plan[op][batched][dtype][variant] = p;
     return TF_OK;
 }
 
@@ -302,7 +316,7 @@ tf_status tf_launch_shape(tf_op op, int batched, tf_dtype dtype, tf_variant vari
     int sms = 0;
     tf_status s = check_device(&sms);
     if (s != TF_OK) return s;
-    const tf_plan p = get_plan(op, batched ? 1 : 0, dtype, variant);
+    const tf_plan p = get_plan(op, batched ? TF_PLAN_BATCHED : flat_class(n), dtype, variant);
     if (block) *block = p.block;
     if (unroll) *unroll = p.unroll;
     if (grid) *grid = batched ? csr_grid(p, sms) : flat_grid(p, n, dtype, sms);
@@ -331,7 +345,8 @@ tf_status tf_tune(tf_op op, int batched, tf_dtype dtype, tf_variant variant, con
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TF_ERR_CUDA;
     float best_ms = 1e30f;
-    tf_plan bp = get_plan(op, batched ? 1 : 0, dtype, variant);
+    const int cls = batched ? TF_PLAN_BATCHED : flat_class(n);
+    tf_plan bp = get_plan(op, cls, dtype, variant);
     tf_status rs = TF_OK;
     for (const tf_plan& p : cands) {
         auto run = [&]() {
@@ -355,7 +370,7 @@ tf_status tf_tune(tf_op op, int batched, tf_dtype dtype, tf_variant variant, con
     {
         std::lock_guard<std::mutex> lk(g_mu);
         init_plans_locked();
-        g_plan[op][batched ? 1 : 0][dtype][variant] = bp;
+        g_plan[op][cls][dtype][variant] = bp;
     }
     if (best) *best = bp;
     return TF_OK;
@@ -369,9 +384,11 @@ tf_status tf_plan_save(const char* path) {
     {
         std::lock_guard<std::mutex> lk(g_mu);
         init_plans_locked();
-        fprintf(f, "# op batched dtype variant block unroll blocks_per_sm tile\n");
+        fprintf(f, "# op class dtype variant block unroll blocks_per_sm tile "
+                   "(class 0 single vector, 1 batched, 2 single vector of at most %d elements)\n",
+                TF_SMALL_N);
         for (int op = 0; op < 2; ++op)
-            for (int b = 0; b < 2; ++b)
+            for (int b = 0; b < kClasses; ++b)
                 for (int dt = 0; dt < 2; ++dt)
                     for (int v = 0; v < kVariants; ++v) {
                         const tf_plan& p = g_plan[op][b][dt][v];
@@ -396,12 +413,12 @@ tf_status tf_plan_load(const char* path) {
         int op, b, dt, v; tf_plan p;
         if (sscanf(line, "%d %d %d %d %d %d %d %d", &op, &b, &dt, &v, &p.block, &p.unroll,
                    &p.blocks_per_sm, &p.tile) != 8 ||
-            op < 0 || op > 1 || b < 0 || b > 1 || dt < 0 || dt > 1 || v < 0 || v >= kVariants ||
-            !plan_valid(p, b, dt)) {
+            op < 0 || op > 1 || b < 0 || b >= kClasses || dt < 0 || dt > 1 || v < 0 ||
+            v >= kVariants || !plan_valid(p, b, dt) || (b != TF_PLAN_BATCHED && p.tile != 0)) {
             rs = TF_ERR_ARG;
             break;
         }
-        rows.push_back({((op * 2 + b) * 2 + dt) * kVariants + v, p});
+        rows.push_back({((op * kClasses + b) * 2 + dt) * kVariants + v, p});
     }
     fclose(f);
     if (rs != TF_OK) return rs;
@@ -409,8 +426,8 @@ tf_status tf_plan_load(const char* path) {
     init_plans_locked();
     for (auto& r : rows) {
         const int k = r.first;
-        g_plan[k / (4 * kVariants)][(k / (2 * kVariants)) % 2][(k / kVariants) % 2]
-              [k % kVariants] = r.second;
+        g_plan[k / (2 * kClasses * kVariants)][(k / (2 * kVariants)) % kClasses]
+              [(k / kVariants) % 2][k % kVariants] = r.second;
     }
     return TF_OK;
 }

@@ -87,8 +87,8 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     G* pieces = reinterpret_cast<G*>(ws + kWsHeader + cnt_bytes);
     const int lane = threadIdx.x & 31;
-    double one = 1.0;                 // binary64 sums: a 1.0 the compiler cannot see
-    if constexpr (sizeof(T) == 8 && !DOT) one = *reinterpret_cast<volatile double*>(&g_one);
+    double one = 1.0;                 // binary64 sums, wide: a 1.0 the compiler cannot see
+    if constexpr ((sizeof(T) == 8 && !DOT) || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const bool bad = *reinterpret_cast<volatile int*>(&hdr->call_bad) != 0;
     if (bad) {

@@ -61,8 +61,8 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     G* pieces = reinterpret_cast<G*>(ws + kWsHeader + cnt_bytes);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double one = 1.0;                 // binary64 sums: a 1.0 the compiler cannot see
-    if constexpr (sizeof(T) == 8 && !DOT) one = *reinterpret_cast<volatile double*>(&g_one);
+    double one = 1.0;                 // binary64 sums, wide: a 1.0 the compiler cannot see
+    if constexpr ((sizeof(T) == 8 && !DOT) || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const uint32_t ring = smem_u32(ring_all) + (uint32_t)(wib * kStages * kStageBytes);
     const uint32_t bar0 = smem_u32(&bars[wib * kStages]);

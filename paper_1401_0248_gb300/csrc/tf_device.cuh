@@ -530,7 +530,8 @@ template <int VAR> constexpr int step_v = VAR == FAST_LIT ? FAST : (VAR == RIG_L
 //   plain:                s = s + y
 //   wide:                 S = S + y in binary64 (binary32 products are exact
 //                         in binary64)
-// `one` is a runtime 1.0 (see dadd): binary64 sums issue their adds as DFMA.
+// `one` is a runtime 1.0 (see dadd): binary64 sums and the binary64
+// accumulator of binary32 data ('wide') issue their adds as DFMA.
 template <int VAR, bool DOT, typename T, typename A>
 __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
     constexpr int STEP = step_v<VAR>;
@@ -546,7 +547,7 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
         } else {
             if (!widen_i(a, p)) p = widen_slow(a);
         }
-        s = __dadd_rn(s, p);
+        s = dadd<true>(s, p, one);      // the widened item (or exact product) by DFMA
     } else if constexpr (VAR == PLAIN) {
         if constexpr (FMA) {
             s = dadd<true>(s, a, one);

@@ -27,6 +27,17 @@ VARIANTS = {"plain": 0, "fast": 1, "rigorous": 2, "wide": 3, "kahan": 4}
 OPS = {"sum": 0, "dot": 1}
 OUT_F64 = 0x1
 DOT_LITERAL = 0x2
+# plan classes (the `batched` argument of the plan calls): single vectors of
+# more than SMALL_N elements, batched calls, single vectors of at most SMALL_N
+PLAN_FLAT, PLAN_BATCHED, PLAN_FLAT_SMALL = 0, 1, 2
+SMALL_N = 1 << 22
+
+
+def plan_class(n, batched=False):
+    """The plan class a call of n elements uses."""
+    if batched:
+        return PLAN_BATCHED
+    return PLAN_FLAT_SMALL if n <= SMALL_N else PLAN_FLAT
 STATUS = {0: "TF_OK", 1: "TF_ERR_ARG", 2: "TF_ERR_DTYPE", 3: "TF_ERR_WORKSPACE",
           4: "TF_ERR_ALIGN", 5: "TF_ERR_CUDA", 6: "TF_ERR_OFFSETS", 7: "TF_ERR_TIMEOUT",
           8: "TF_ERR_UNSUPPORTED"}
@@ -300,6 +311,9 @@ def dot_host(x, y, variant="fast", *, out_f64=False, x_dev=None, y_dev=None, ws=
 
 # ------------------------------------------------------------------- plans
 def plan_get(op="sum", batched=False, dtype=torch.float32, variant="fast"):
+    """The plan of a key; `batched` is the plan class (False/0 single vectors of
+    more than SMALL_N elements, True/1 batched, 2 single vectors of at most
+    SMALL_N elements; plan_class(n) gives the one a call uses)."""
     p = Plan()
     _check("tf_plan_get", lib().tf_plan_get(OPS[op], int(batched), DTYPES[dtype], VARIANTS[variant],
                                             C.byref(p)))

@@ -82,6 +82,17 @@ def test_plan_save_load_roundtrip(tmp_path):
         f.write("0 0 0 1 100 1 1 0\n")
     with pytest.raises(twofold.TwofoldError):
         twofold.plan_load(path)
+    # the small single-vector class keeps its own plans
+    small = twofold.plan_get("sum", twofold.PLAN_FLAT_SMALL, torch.float64, "fast")
+    twofold.plan_set("sum", twofold.PLAN_FLAT_SMALL, torch.float64, "fast", 128, 1, 4)
+    assert twofold.plan_get("sum", twofold.PLAN_FLAT_SMALL, torch.float64, "fast")["block"] == 128
+    path2 = str(tmp_path / "plans2.txt")
+    twofold.plan_save(path2)
+    assert any(line.startswith("0 2 1 1 128 1 4 0") for line in open(path2))
+    twofold.plan_set("sum", twofold.PLAN_FLAT_SMALL, torch.float64, "fast", small["block"],
+                     small["unroll"], small["blocks_per_sm"])
+    assert twofold.plan_class(1 << 22) == 2 and twofold.plan_class((1 << 22) + 1) == 0
+    assert twofold.plan_class(5, batched=True) == 1
 
 
 def test_product_path_has_no_cpu_fallback():

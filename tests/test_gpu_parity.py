@@ -350,13 +350,15 @@ def test_flat_every_plan_shape(block, unroll, bps):
     for dt in ("f32", "f64"):
         x = I.uniform(n, dt, seed=9, device=DEV)
         y = I.uniform(n, dt, seed=9, stream=1, device=DEV)
+        cls = tf.plan_class(n)
         for op, variant in VARIANTS:
-            before = tf.plan_get(op, False, TD[dt], variant)
+            before = tf.plan_get(op, cls, TD[dt], variant)
             try:
-                tf.plan_set(op, False, TD[dt], variant, block, unroll, bps)
+                tf.plan_set(op, cls, TD[dt], variant, block, unroll, bps)
+                assert tf.launch_shape(op, False, TD[dt], variant, n)[:2] == (block, unroll)
                 check_flat(op, variant, dt, x, y if op == "dot" else None)
             finally:
-                tf.plan_set(op, False, TD[dt], variant, before["block"], before["unroll"],
+                tf.plan_set(op, cls, TD[dt], variant, before["block"], before["unroll"],
                             before["blocks_per_sm"])
 
 
@@ -557,16 +559,21 @@ def test_host_buffer_calls_match_device_calls():
         assert (v, e) == (d[0], d[1])
 
 
-def test_tuner_picks_a_valid_plan_and_stays_exact():
-    n = 1 << 22
+@pytest.mark.parametrize("n", [1 << 20, (1 << 22) + 1])
+def test_tuner_picks_a_valid_plan_and_stays_exact(n):
+    """tf_tune stores its choice in the plan class of n (small or large)."""
     x = I.uniform(n, "f32", seed=15, device=DEV)
-    before = tf.plan_get("sum", False, torch.float32, "rigorous")
+    cls = tf.plan_class(n)
+    other = tf.PLAN_FLAT if cls == tf.PLAN_FLAT_SMALL else tf.PLAN_FLAT_SMALL
+    before = tf.plan_get("sum", cls, torch.float32, "rigorous")
+    untouched = tf.plan_get("sum", other, torch.float32, "rigorous")
     try:
         p = tf.tune("sum", "rigorous", x, reps=2)
-        assert p == tf.plan_get("sum", False, torch.float32, "rigorous")
+        assert p == tf.plan_get("sum", cls, torch.float32, "rigorous")
+        assert tf.plan_get("sum", other, torch.float32, "rigorous") == untouched
         check_flat("sum", "rigorous", "f32", x, None)
     finally:
-        tf.plan_set("sum", False, torch.float32, "rigorous", before["block"], before["unroll"],
+        tf.plan_set("sum", cls, torch.float32, "rigorous", before["block"], before["unroll"],
                     before["blocks_per_sm"])
 
 
