@@ -35,18 +35,50 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
     // steps of U full vectors: vector j + u*P is step m = kU + u, chain u*V + l
-    for (; j + (U - 1) * P < nv; j += U * P) {
-        T xv[U][V], yv[U][V];
+    auto load = [&](int64_t jj, T (&xv)[U][V], T (&yv)[U][V]) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            ld_vec<T, V>(x + (j + u * P) * V, aligned, xv[u]);
-            if constexpr (DOT) ld_vec<T, V>(y + (j + u * P) * V, aligned, yv[u]);
+            ld_vec<T, V>(x + (jj + u * P) * V, aligned, xv[u]);
+            if constexpr (DOT) ld_vec<T, V>(y + (jj + u * P) * V, aligned, yv[u]);
         }
+    };
+    auto feed_all = [&](const T (&xv)[U][V], const T (&yv)[U][V]) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int l = 0; l < V; ++l)
                 feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[u][l], DOT ? yv[u][l] : T(0), one);
+    };
+    // binary32 twofold dots: the next step's loads go out before this step's
+    // arithmetic (two arrays in flight per thread instead of one)
+    constexpr bool PREFETCH = sizeof(T) == 4 && DOT && VAR != WIDE;
+    if constexpr (PREFETCH) {
+        if (j + (U - 1) * P < nv) {
+            T xv[U][V], yv[U][V];
+            load(j, xv, yv);
+            for (;;) {
+                const int64_t jn = j + U * P;
+                const bool more = jn + (U - 1) * P < nv;
+                T xn[U][V], yn[U][V];
+                if (more) load(jn, xn, yn);
+                feed_all(xv, yv);
+                j = jn;
+                if (!more) break;
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int l = 0; l < V; ++l) {
+                        xv[u][l] = xn[u][l];
+                        yv[u][l] = yn[u][l];
+                    }
+            }
+        }
+    } else {
+        for (; j + (U - 1) * P < nv; j += U * P) {
+            T xv[U][V], yv[U][V];
+            load(j, xv, yv);
+            feed_all(xv, yv);
+        }
     }
     // fewer than U full vectors left for this thread, and maybe the partial
     // vector n/V (owned by the thread with g = (n/V) mod P)
