@@ -5,6 +5,8 @@
 #include "twofold.h"
 #include "tf_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -114,6 +116,15 @@ size_t flat_ws_bytes() { return kHeaderBytes + tf::kPairBytes * (size_t)tf::kMax
 
 size_t esize(int dtype) { return dtype == 0 ? 4 : 8; }
 
+// One NVTX range per API call (a no-op unless a profiler is attached), so
+// that timelines show the library's calls around its kernels.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
+
 // the kernels' variant: the literal dot forms are variants 5 and 6 there
 int kernel_variant(int op, int variant, uint32_t flags) {
     if (op == 1 && (flags & TF_DOT_LITERAL) && (variant == TF_FAST || variant == TF_RIGOROUS))
@@ -204,18 +215,21 @@ int32_t tf_device_sm_count(void) {
 
 tf_status tf_sum(const void* x, int64_t n, tf_dtype dtype, tf_variant variant, void* out,
                  void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream) {
+    Range r("tf_sum");
     return run_flat(0, x, nullptr, n, dtype, variant, out, ws, ws_bytes, flags,
                     (cudaStream_t)stream);
 }
 
 tf_status tf_dot(const void* x, const void* y, int64_t n, tf_dtype dtype, tf_variant variant,
                  void* out, void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream) {
+    Range r("tf_dot");
     return run_flat(1, x, y, n, dtype, variant, out, ws, ws_bytes, flags, (cudaStream_t)stream);
 }
 
 tf_status tf_sum_batched(const void* x, int64_t n, const int64_t* offsets, int64_t nseg,
                          tf_dtype dtype, tf_variant variant, void* out, void* ws,
                          size_t ws_bytes, uint32_t flags, tf_stream_t stream) {
+    Range r("tf_sum_batched");
     return run_csr(0, x, nullptr, n, offsets, nseg, dtype, variant, out, ws, ws_bytes, flags,
                    (cudaStream_t)stream);
 }
@@ -223,6 +237,7 @@ tf_status tf_sum_batched(const void* x, int64_t n, const int64_t* offsets, int64
 tf_status tf_dot_batched(const void* x, const void* y, int64_t n, const int64_t* offsets,
                          int64_t nseg, tf_dtype dtype, tf_variant variant, void* out,
                          void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream) {
+    Range r("tf_dot_batched");
     return run_csr(1, x, y, n, offsets, nseg, dtype, variant, out, ws, ws_bytes, flags,
                    (cudaStream_t)stream);
 }
@@ -251,6 +266,7 @@ static tf_status host_call(int op, const void* xh, const void* yh, int64_t n, in
 tf_status tf_sum_host(const void* x_host, int64_t n, tf_dtype dtype, tf_variant variant,
                       void* out_host, void* x_dev, void* ws, size_t ws_bytes, uint32_t flags,
                       tf_stream_t stream) {
+    Range r("tf_sum_host");
     return host_call(0, x_host, nullptr, n, dtype, variant, out_host, x_dev, nullptr, ws,
                      ws_bytes, flags, (cudaStream_t)stream);
 }
@@ -258,6 +274,7 @@ tf_status tf_sum_host(const void* x_host, int64_t n, tf_dtype dtype, tf_variant 
 tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtype dtype,
                       tf_variant variant, void* out_host, void* x_dev, void* y_dev, void* ws,
                       size_t ws_bytes, uint32_t flags, tf_stream_t stream) {
+    Range r("tf_dot_host");
     return host_call(1, x_host, y_host, n, dtype, variant, out_host, x_dev, y_dev, ws, ws_bytes,
                      flags, (cudaStream_t)stream);
 }

@@ -363,6 +363,41 @@ def test_flat_every_plan_shape(block, unroll, bps):
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("blocks", [1, 2, 3, 7])
+def test_flat_last_block_done_with_few_blocks(dt, blocks):
+    """The last-block-done grid fold with 1, 2 and odd block counts (and a
+    partial last vector), bit for bit against the replay."""
+    V = 4 if dt == "f32" else 2
+    n = 128 * V * blocks - (V - 1)
+    cls = tf.plan_class(n)
+    x = I.normal(n, dt, seed=blocks, device=DEV)
+    y = I.normal(n, dt, seed=blocks, stream=2, device=DEV)
+    for op, variant in (("sum", "rigorous"), ("dot", "fast"), ("sum", "kahan")):
+        before = tf.plan_get(op, cls, TD[dt], variant)
+        try:
+            tf.plan_set(op, cls, TD[dt], variant, 128, 1, 8)
+            assert tf.launch_shape(op, False, TD[dt], variant, n)[2] == blocks
+            check_flat(op, variant, dt, x, y if op == "dot" else None)
+        finally:
+            tf.plan_set(op, cls, TD[dt], variant, before["block"], before["unroll"],
+                        before["blocks_per_sm"])
+
+
+def test_flat_partial_sums_overflow_with_finite_exact_sum():
+    """Partial sums that overflow while the exact sum is 0: the result follows
+    the documented order (Inf/NaN where its additions overflow), matching the
+    replay; reported, not bound-checked."""
+    big = np.full(4096, 1.5e308)
+    x = np.concatenate([big, -big])
+    xt = torch.from_numpy(x).to(DEV)
+    for variant in ("fast", "rigorous", "plain"):
+        check_flat("sum", variant, "f64", xt, None)
+    xi = torch.from_numpy(np.ascontiguousarray(np.stack([big, -big], 1).reshape(-1))).to(DEV)
+    for variant in ("fast", "rigorous"):
+        check_flat("sum", variant, "f64", xi, None)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
 def test_flat_misaligned_pointers_same_bits(dt):
     n = 200003
     base = I.normal(n + 3, dt, seed=4, device=DEV)
