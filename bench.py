@@ -540,7 +540,7 @@ def run_batched(args, dev, stream):
     """The ragged-batch configuration beside the step: 16,384 binary32 CSR
     segments with log-uniform lengths in [16, 2^18] (uniform [-1, 1) data),
     each call one offsets check plus one persistent launch, replayed from a
-    CUDA graph."""
+    CUDA graph; the twofold binary64 forms of the same layout beside it."""
     import torch
     from paper_1401_0248_gb300 import inputs as I
     from paper_1401_0248_gb300 import twofold as tf
@@ -548,17 +548,28 @@ def run_batched(args, dev, stream):
     L = I.csr_lengths(nseg, 16, 1 << 18, seed=0)
     off_h = I.csr_offsets(L)
     n = int(off_h[-1])
-    x = I.uniform(n, "f32", seed=1, device=dev)
-    y = I.uniform(n, "f32", seed=1, stream=1, device=dev)
     off = torch.from_numpy(off_h).to(dev)
     hbm, _ = load_peaks()
-    res = {"config": "16384 f32 segments, lengths log-uniform [16, 2^18], %d elements" % n,
+    res = {"config": "16384 segments, lengths log-uniform [16, 2^18], %d elements; "
+                     "binary32 (the configuration) and binary64 (beside it)" % n,
            "graph": True, "kernels": {}}
+    for dt, td, variants in (("f32", torch.float32, ("plain", "fast", "rigorous")),
+                             ("f64", torch.float64, ("fast", "rigorous"))):
+        x = I.uniform(n, dt, seed=1, device=dev)
+        y = I.uniform(n, dt, seed=1, stream=1, device=dev)
+        _batched_kernels(args, tf, dev, stream, res, dt, td, variants, x, y, off, n, nseg, hbm)
+        del x, y
+        torch.cuda.empty_cache()
+    return res
+
+
+def _batched_kernels(args, tf, dev, stream, res, dt, td, variants, x, y, off, n, nseg, hbm):
+    import torch
     for op in OPS:
-        for v in ("plain", "fast", "rigorous"):
-            ws = torch.zeros(tf.workspace_size(op, True, torch.float32, v, n, nseg),
+        for v in variants:
+            ws = torch.zeros(tf.workspace_size(op, True, td, v, n, nseg),
                              dtype=torch.uint8, device=dev)
-            out = torch.empty(nseg, 2, device=dev)
+            out = torch.empty(nseg, 2, dtype=td, device=dev)
             if op == "sum":
                 call = (lambda v=v, ws=ws, out=out: tf.sum_batched(x, off, v, ws=ws, out=out))
             else:
@@ -583,12 +594,11 @@ def run_batched(args, dev, stream):
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / reps
-            byts = nbytes("f32", op, n) + 8 * (nseg + 1) + 8 * nseg
+            byts = nbytes(dt, op, n) + 8 * (nseg + 1) + 2 * (4 if dt == "f32" else 8) * nseg
             gbs = byts / (ms * 1e-3) / 1e9
-            res["kernels"]["f32_%s_%s" % (op, v)] = {"ms": round(ms, 4), "gbs": round(gbs, 1),
-                                                     "frac_hbm": round(gbs / hbm, 4)}
+            res["kernels"]["%s_%s_%s" % (dt, op, v)] = {"ms": round(ms, 4), "gbs": round(gbs, 1),
+                                                        "frac_hbm": round(gbs / hbm, 4)}
             del g
-    return res
 
 
 def gpu_numa_cpus(dev):
