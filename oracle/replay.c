@@ -64,10 +64,13 @@
  *   lane q mod 32, chain ((floor(q/32)) mod U)*V + (r mod V).  Lanes fold
  *   their chains by the tree above and the 32 lanes by the butterfly.  A
  *   segment that lies in one tile outputs its piece pair.  A segment over k
- *   tiles merges its k piece pairs (binary64 for binary32 data, except plain)
- *   as lane l = 0..31 starting from piece l (identity if l >= k) and merging
- *   pieces l+32, l+64, ... in turn, then the butterfly; the output rule above
- *   applies.  An empty segment outputs (+0, +0).
+ *   tiles merges its k piece pairs (binary64 for binary32 data, except plain):
+ *   for k <= 32 as 32 lanes holding pieces 0..k-1 (+0 pairs after them)
+ *   folded by the butterfly; for k > 32 by a pairwise tree in tile order:
+ *   with w = 1, 2, 4, ..., the pair at piece j (j a multiple of 2w) becomes
+ *   merge(pair j, pair j + w) when j + w < k and stays as it is otherwise;
+ *   the root is piece 0's pair.  The output rule above applies.  An empty
+ *   segment outputs (+0, +0).
  */
 #include "oracle.h"
 #include "orc_internal.h"
@@ -207,18 +210,12 @@ static pr_t butterfly(int f, int tw, pr_t* v, int W) {
     return v[0];
 }
 
-/* fold of k pairs by 32 lanes: lane l takes l, l+32, ..., then butterfly */
-static pr_t lane_fold(int f, int tw, const pr_t* p, int64_t k, int lanes) {
-    pr_t v[32];
-    for (int l = 0; l < lanes; ++l) {
-        pr_t a = { 0.0, 0.0, 0 };
-        if (l < k) {
-            a = p[l];
-            for (int64_t i = l + lanes; i < k; i += lanes) a = merge(f, tw, a, p[i]);
-        }
-        v[l] = a;
-    }
-    return butterfly(f, tw, v, lanes);
+/* pairwise tree over k pairs in order: pair j (j a multiple of 2w) takes
+   pair j + w for w = 1, 2, 4, ... while j + w < k; the result is pair 0 */
+static pr_t pair_tree(int f, int tw, pr_t* p, int64_t k) {
+    for (int64_t w = 1; w < k; w *= 2)
+        for (int64_t j = 0; j + w < k; j += 2 * w) p[j] = merge(f, tw, p[j], p[j + w]);
+    return p[0];
 }
 
 static void write_out(const prob_t* P, pr_t r, int out_f64, void* out) {
@@ -336,8 +333,18 @@ static void replay_segment(const cjob_t* J, int64_t s) {
             int64_t hi = b < (w + 1) * J->tile ? b : (w + 1) * J->tile;
             pcs[w - w0] = piece_pair(P, lo, hi, w * J->tile, J->unroll);
         }
-        if (k == 1) res = pcs[0];
-        else res = lane_fold(f_grid(P), twofold(P), pcs, k, 32);
+        if (k == 1) {
+            res = pcs[0];
+        } else if (k <= 32) {
+            pr_t lanes[32];
+            for (int l = 0; l < 32; ++l) {
+                pr_t z = { 0.0, 0.0, 0 };
+                lanes[l] = l < k ? pcs[l] : z;
+            }
+            res = butterfly(f_grid(P), twofold(P), lanes, 32);
+        } else {
+            res = pair_tree(f_grid(P), twofold(P), pcs, k);
+        }
         free(pcs);
     }
     write_out(P, res, J->out_f64, o);

@@ -10,12 +10,13 @@
 // tile, slot m feeding chains (m mod U)*V + (element mod V).  Elements
 // outside the piece are fed as +0, which leaves a twofold, plain or wide
 // chain's bits unchanged (Kahan chains skip them), so the chain assignment is
-// the documented one.  A segment inside one tile is written directly; a
-// segment over k tiles leaves k piece pairs in the workspace and the warp that
-// completes the k-th piece (a per-segment ticket, no waiting) merges them in
-// tile order, so which warp reduces which tile never changes a bit.  A first
-// small kernel checks the offsets, clears the tickets, writes the empty
-// segments and records the segment holding each tile's first element.
+// the documented one.  A segment inside one tile is written directly; the k
+// pieces of a segment over k tiles merge by a pairwise tree in tile order,
+// each merge done by the warp that completes the second of its two children
+// (arrival counters, no waiting), so which warp reduces which tile never
+// changes a bit.  A first small kernel checks the offsets, clears the
+// counters, writes the empty segments and records the segment holding each
+// tile's first element.
 #include "tf_csr.cuh"
 
 namespace tf {
@@ -23,8 +24,9 @@ namespace tf {
 constexpr int kTfErrOffsets = 6;       // TF_ERR_OFFSETS
 
 size_t csr_ws_bytes(int64_t n, int64_t nseg) {
+    (void)nseg;
     const size_t ntiles = csr_max_tiles(n);
-    return kHeaderBytes + csr_cnt_bytes(nseg) + ntiles * 2 * kPairBytes + ntiles * 8;
+    return kHeaderBytes + csr_cnt_bytes(n) + ntiles * 2 * kPairBytes + ntiles * 8;
 }
 
 template <typename T, int VAR>
@@ -43,7 +45,6 @@ __global__ void csr_prepare(const int64_t* __restrict__ off, int64_t nseg, int64
         if (s < nseg) {
             const int64_t b = off[s + 1];
             bad |= (b < a);
-            cnt[s] = 0u;
             if (b == a) write_out<T, VAR, G>(out, s, G(0), G(0), out_f64 != 0);
         }
     }
@@ -52,6 +53,8 @@ __global__ void csr_prepare(const int64_t* __restrict__ off, int64_t nseg, int64
     // offsets the map is not used)
     const int64_t ntiles = (n + tile - 1) / tile;
     for (int64_t t = first; t < ntiles; t += stride) {
+        cnt[2 * t] = 0u;                      // the arrival counters of the tile's two slots
+        cnt[2 * t + 1] = 0u;
         const int64_t pos = t * tile;
         int64_t lo = 0, hi = nseg;
         while (hi - lo > 1) {
@@ -243,7 +246,7 @@ static cudaError_t launch_u(int unroll, const void* x, const void* y, int64_t n,
                             int out_f64, cudaStream_t st) {
     (void)ws_bytes;
     unsigned char* w = static_cast<unsigned char*>(ws);
-    const size_t cnt_bytes = csr_cnt_bytes(nseg);
+    const size_t cnt_bytes = csr_cnt_bytes(n);
     int64_t* tile_seg = reinterpret_cast<int64_t*>(w + kHeaderBytes + cnt_bytes +
                                                    csr_max_tiles(n) * 2 * kPairBytes);
     const int64_t items = std::max<int64_t>(nseg + 1, (n + tile - 1) / tile);

@@ -6,18 +6,28 @@
 
 namespace tf {
 
-// workspace: header | per-segment tickets | two piece slots per tile | tile map
-inline size_t csr_cnt_bytes(int64_t nseg) {
-    return ((size_t)(nseg > 0 ? nseg : 1) * 4 + 255) / 256 * 256;
-}
+// workspace: header | one arrival counter per piece slot | two piece slots
+// per tile | tile map.  Sized for the smallest tile (kMinTile).
 inline size_t csr_max_tiles(int64_t n) { return (size_t)((n + kMinTile - 1) / kMinTile) + 1; }
+inline size_t csr_cnt_bytes(int64_t n) { return (csr_max_tiles(n) * 2 * 4 + 255) / 256 * 256; }
+
+// piece i of a segment whose first tile is w0: slot 2*w0 + 1 for i = 0 (the
+// piece that starts the segment), 2*(w0 + i) after it
+__device__ __forceinline__ int64_t piece_slot(int64_t w0, int64_t i) {
+    return i == 0 ? 2 * w0 + 1 : 2 * (w0 + i);
+}
 
 // The piece [max(a, tlo), min(b, thi)) of segment s = [a, b) in tile t has
 // been fed into the warp's C chains per lane: fold the chains (tree), the
 // lanes (butterfly), then either write the segment (it lies in this tile) or
-// store the piece's pair in slot 2t (2t + 1 for the segment's first piece)
-// and take the segment's ticket; the warp completing the k-th piece merges
-// the k pairs in tile order (lane l takes pieces l, l + 32, ...).
+// merge the segment's k pieces in tile order.  Up to 32 pieces: the warp that
+// completes the last one merges them across its lanes (lane l takes piece l,
+// then the butterfly).  More: a pairwise tree, the node over pieces
+// [j, j + 2w) being merge(node [j, j + w), node [j + w, j + 2w)), or the left
+// node alone when j + w >= k; each merge is done by whichever warp completes
+// the second of the two children (an arrival counter per node, no waiting),
+// so no warp does more than log2(k) merges.  The bits do not depend on which
+// warp does them.
 template <typename T, int VAR, int C>
 __device__ __forceinline__ void piece_finish(typename Acc<T, VAR>::type (&cs)[C],
                                              typename Acc<T, VAR>::type (&ce)[C], int64_t s,
@@ -41,45 +51,69 @@ __device__ __forceinline__ void piece_finish(typename Acc<T, VAR>::type (&cs)[C]
         if (lane == 0) write_out<T, VAR, G>(out, s, (G)pv, (G)pe, out_f64 != 0);
         return;
     }
-    const int64_t w0 = a / tile, w1 = (b - 1) / tile;
-    const int64_t k = w1 - w0 + 1;
-    const int64_t slot = (a < tlo) ? 2 * t : 2 * t + 1;
-    unsigned int old = 0;
-    if (lane == 0) {
-        pieces[2 * slot] = (G)pv;
-        pieces[2 * slot + 1] = (G)pe;
+    const int64_t w0 = a / tile, k = (b - 1) / tile - w0 + 1;
+    G gv = (G)pv, ge = (G)pe;                   // the node [st, st + w) in registers
+    if (k <= 32) {
+        // up to 32 pieces: the warp completing the k-th (a ticket on the first
+        // piece's counter, which the tree below never uses) merges them, lane l
+        // taking piece l, then the butterfly
+        unsigned int* ticket = &cnt[piece_slot(w0, 0)];
+        unsigned int old = 0;
+        if (lane == 0) {
+            G* mine = pieces + 2 * piece_slot(w0, t - w0);
+            mine[0] = gv;
+            mine[1] = ge;
+            __threadfence();
+            old = atomicAdd(ticket, 1u);
+        }
+        old = __shfl_sync(FULL, old, 0);
+        if ((int64_t)old != k - 1) return;
         __threadfence();
-        old = atomicAdd(&cnt[s], 1u);
-    }
-    old = __shfl_sync(FULL, old, 0);
-    if ((int64_t)old != k - 1) return;
-    // last piece of the segment: merge the k pieces in tile order
-    __threadfence();
-    G gv = G(0), ge = G(0);
-    if (lane < k) {
-        const int64_t s0 = (lane == 0) ? 2 * w0 + 1 : 2 * (w0 + lane);
-        ld_pair_cg(pieces + 2 * s0, gv, ge);
-        // the merges form one chain per lane; the loads do not depend on
-        // them, so fetch 8 pieces at a time
-        constexpr int B = 8;
-        int64_t i = lane + 32;
-        for (; i + 32 * (B - 1) < k; i += 32 * B) {
-            G v2[B], e2[B];
-#pragma unroll
-            for (int j = 0; j < B; ++j) ld_pair_cg(pieces + 2 * (2 * (w0 + i + 32 * j)), v2[j], e2[j]);
-#pragma unroll
-            for (int j = 0; j < B; ++j) merge<TW>(gv, ge, v2[j], e2[j]);
+        G lv = G(0), le = G(0);
+        if (lane < k) ld_pair_cg(pieces + 2 * piece_slot(w0, lane), lv, le);
+        warp_fold<TW>(lv, le);
+        if (lane == 0) {
+            write_out<T, VAR, G>(out, s, lv, le, out_f64 != 0);
+            *ticket = 0u;
         }
-        for (; i < k; i += 32) {
-            G v2, e2;
-            ld_pair_cg(pieces + 2 * (2 * (w0 + i)), v2, e2);
+        return;
+    }
+    int64_t st = t - w0, w = 1;
+    for (;;) {
+        if (st == 0 && w >= k) {                // the root: the whole segment
+            if (lane == 0) write_out<T, VAR, G>(out, s, gv, ge, out_f64 != 0);
+            return;
+        }
+        const bool left = ((st / w) & 1) == 0;
+        if (left && st + w >= k) {              // no right sibling: the parent is this node
+            w *= 2;
+            continue;
+        }
+        const int64_t sib = left ? st + w : st - w;
+        unsigned int* ctr = &cnt[piece_slot(w0, left ? sib : st)];   // keyed by the right child
+        unsigned int old = 0;
+        if (lane == 0) {
+            G* mine = pieces + 2 * piece_slot(w0, st);
+            mine[0] = gv;
+            mine[1] = ge;
+            __threadfence();
+            old = atomicAdd(ctr, 1u);
+        }
+        old = __shfl_sync(FULL, old, 0);
+        if (old == 0u) return;                  // the sibling's warp completes the parent
+        __threadfence();
+        G v2, e2;
+        ld_pair_cg(pieces + 2 * piece_slot(w0, sib), v2, e2);
+        if (left) {
             merge<TW>(gv, ge, v2, e2);
+        } else {
+            merge<TW>(v2, e2, gv, ge);
+            gv = v2;
+            ge = e2;
+            st = sib;
         }
-    }
-    warp_fold<TW>(gv, ge);
-    if (lane == 0) {
-        write_out<T, VAR, G>(out, s, gv, ge, out_f64 != 0);
-        cnt[s] = 0u;
+        if (lane == 0) *ctr = 0u;               // ready for the next call
+        w *= 2;
     }
 }
 

@@ -216,20 +216,31 @@ def compose_csr(op, variant, x, y, off, unroll, tile, out_f64=False):
             lanes = [ab.tree([chain_pair(op, variant, x, y, np.array(li, dtype=np.int64))
                               for li in lists[l]]) for l in range(32)]
             pcs.append(ab.butterfly(lanes))
-        if len(pcs) == 1:
-            res = pcs[0]
-        else:
-            lanes = []
-            for l in range(32):
-                acc = (0.0, 0.0)
-                if l < len(pcs):
-                    acc = pcs[l]
-                    for i in range(l + 32, len(pcs), 32):
-                        acc = ag.merge(acc, pcs[i])
-                lanes.append(acc)
-            res = ag.butterfly(lanes)
+        res = piece_merge(ag, pcs, (0.0, 0.0))
         outs.append(out_pair(dt, variant, res, out_f64))
     return np.array(outs)
+
+
+def piece_merge(ar, pcs, zero):
+    """up to 32 pieces: one per lane (zero pairs after them), the butterfly;
+    more: the pairwise tree"""
+    if len(pcs) == 1:
+        return pcs[0]
+    if len(pcs) <= 32:
+        return ar.butterfly(list(pcs) + [zero] * (32 - len(pcs)))
+    return pair_tree(ar, pcs)
+
+
+def pair_tree(ar, pcs):
+    """pieces merged as a complete binary tree over their tile order, written
+    top-down: the node over [lo, hi) merges its halves [lo, mid), [mid, hi)
+    with mid = lo + the largest power of two below hi - lo"""
+    def node(lo, hi):
+        if hi - lo == 1:
+            return pcs[lo]
+        half = 1 << ((hi - lo - 1).bit_length() - 1)
+        return ar.merge(node(lo, lo + half), node(lo + half, hi))
+    return node(0, len(pcs))
 
 
 @pytest.mark.parametrize("op,variant,dt,unroll,tile", [
@@ -249,6 +260,23 @@ def test_replay_csr_matches_composition(op, variant, dt, unroll, tile):
     y = I.normal(n, s, seed=6, stream=2).numpy() if op == "dot" else None
     want = compose_csr(op, variant, x, y, off, unroll, tile)
     got = O.replay_csr(op, variant, x, off, y, unroll=unroll, tile=tile, nthreads=3)
+    assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
+
+
+@pytest.mark.parametrize("op,variant,dt", [("sum", "rigorous", np.float64),
+                                           ("dot", "fast", np.float32),
+                                           ("sum", "plain", np.float32)])
+def test_replay_csr_long_segments_tree(op, variant, dt):
+    """segments over more than 32 tiles merge their pieces by the pairwise
+    tree (33, 64 and 77 pieces, beside short ones)"""
+    tile = 128
+    L = [5, 33 * tile - 7, 9, 64 * tile, 77 * tile + 13, 3]
+    off = I.csr_offsets(L)
+    s = "f32" if dt == np.float32 else "f64"
+    x = I.normal(int(off[-1]), s, seed=12).numpy()
+    y = I.normal(int(off[-1]), s, seed=12, stream=3).numpy() if op == "dot" else None
+    want = compose_csr(op, variant, x, y, off, 1, tile)
+    got = O.replay_csr(op, variant, x, off, y, unroll=1, tile=tile, nthreads=2)
     assert np.array_equal(got.view(np.uint8), want.view(np.uint8))
 
 
@@ -401,6 +429,7 @@ def test_replay_csr_binary128_matches_composition():
     from fractions import Fraction
     L = I.csr_lengths(12, 3, 400, seed=15)
     L[4] = 0
+    L[7] = 40 * 64 + 5                          # a segment over 41 tiles: the tree
     off = I.csr_offsets(L)
     n, unroll, tile = int(off[-1]), 2, 64
     ic = I.ill_conditioned(n, "f64", 1e28, seed=16)
@@ -418,20 +447,7 @@ def test_replay_csr_binary128_matches_composition():
                 lists[(r // 2) % 32][((r // 64) % unroll) * 2 + r % 2].append(i)
             pcs.append(q.butterfly([q.tree([chain_q(x, None, li) for li in lists[l]])
                                     for l in range(32)]))
-        if not pcs:
-            res = Fraction(0)
-        elif len(pcs) == 1:
-            res = pcs[0]
-        else:
-            lanes = []
-            for l in range(32):
-                acc = Fraction(0)
-                if l < len(pcs):
-                    acc = pcs[l]
-                    for i in range(l + 32, len(pcs), 32):
-                        acc = q.merge(acc, pcs[i])
-                lanes.append(acc)
-            res = q.butterfly(lanes)
+        res = piece_merge(q, pcs, Fraction(0)) if pcs else Fraction(0)
         want.append(out_q(res))
     got = O.replay_csr("sum", "wide", x, off, unroll=unroll, tile=tile)
     assert np.array_equal(got.view(np.uint8), np.array(want).view(np.uint8))
