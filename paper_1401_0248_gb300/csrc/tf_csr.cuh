@@ -17,6 +17,57 @@ __device__ __forceinline__ int64_t piece_slot(int64_t w0, int64_t i) {
     return i == 0 ? 2 * w0 + 1 : 2 * (w0 + i);
 }
 
+// The pairwise tree of a segment's k > 32 pieces (see piece_finish), from
+// the piece at index st whose pair (gv, ge) the warp holds.  Out of line: the
+// streaming loops that call piece_finish keep their registers.
+template <typename T, int VAR>
+static __device__ __noinline__ void piece_tree(typename GridAcc<T, VAR>::type gv,
+                                               typename GridAcc<T, VAR>::type ge, int64_t st,
+                                               int64_t w0, int64_t k, int64_t s,
+                                               unsigned int* cnt,
+                                               typename GridAcc<T, VAR>::type* pieces,
+                                               int lane, void* out, int out_f64) {
+    using G = typename GridAcc<T, VAR>::type;
+    constexpr bool TW = twofold_v<VAR>;
+    int64_t w = 1;
+    for (;;) {
+        if (st == 0 && w >= k) {                // the root: the whole segment
+            if (lane == 0) write_out<T, VAR, G>(out, s, gv, ge, out_f64 != 0);
+            return;
+        }
+        const bool left = ((st / w) & 1) == 0;
+        if (left && st + w >= k) {              // no right sibling: the parent is this node
+            w *= 2;
+            continue;
+        }
+        const int64_t sib = left ? st + w : st - w;
+        unsigned int* ctr = &cnt[piece_slot(w0, left ? sib : st)];   // keyed by the right child
+        unsigned int old = 0;
+        if (lane == 0) {
+            G* mine = pieces + 2 * piece_slot(w0, st);
+            mine[0] = gv;
+            mine[1] = ge;
+            __threadfence();
+            old = atomicAdd(ctr, 1u);
+        }
+        old = __shfl_sync(FULL, old, 0);
+        if (old == 0u) return;                  // the sibling's warp completes the parent
+        __threadfence();
+        G v2, e2;
+        ld_pair_cg(pieces + 2 * piece_slot(w0, sib), v2, e2);
+        if (left) {
+            merge<TW>(gv, ge, v2, e2);
+        } else {
+            merge<TW>(v2, e2, gv, ge);
+            gv = v2;
+            ge = e2;
+            st = sib;
+        }
+        if (lane == 0) *ctr = 0u;               // ready for the next call
+        w *= 2;
+    }
+}
+
 // The piece [max(a, tlo), min(b, thi)) of segment s = [a, b) in tile t has
 // been fed into the warp's C chains per lane: fold the chains (tree), the
 // lanes (butterfly), then either write the segment (it lies in this tile) or
@@ -78,43 +129,7 @@ __device__ __forceinline__ void piece_finish(typename Acc<T, VAR>::type (&cs)[C]
         }
         return;
     }
-    int64_t st = t - w0, w = 1;
-    for (;;) {
-        if (st == 0 && w >= k) {                // the root: the whole segment
-            if (lane == 0) write_out<T, VAR, G>(out, s, gv, ge, out_f64 != 0);
-            return;
-        }
-        const bool left = ((st / w) & 1) == 0;
-        if (left && st + w >= k) {              // no right sibling: the parent is this node
-            w *= 2;
-            continue;
-        }
-        const int64_t sib = left ? st + w : st - w;
-        unsigned int* ctr = &cnt[piece_slot(w0, left ? sib : st)];   // keyed by the right child
-        unsigned int old = 0;
-        if (lane == 0) {
-            G* mine = pieces + 2 * piece_slot(w0, st);
-            mine[0] = gv;
-            mine[1] = ge;
-            __threadfence();
-            old = atomicAdd(ctr, 1u);
-        }
-        old = __shfl_sync(FULL, old, 0);
-        if (old == 0u) return;                  // the sibling's warp completes the parent
-        __threadfence();
-        G v2, e2;
-        ld_pair_cg(pieces + 2 * piece_slot(w0, sib), v2, e2);
-        if (left) {
-            merge<TW>(gv, ge, v2, e2);
-        } else {
-            merge<TW>(v2, e2, gv, ge);
-            gv = v2;
-            ge = e2;
-            st = sib;
-        }
-        if (lane == 0) *ctr = 0u;               // ready for the next call
-        w *= 2;
-    }
+    piece_tree<T, VAR>(gv, ge, t - w0, w0, k, s, cnt, pieces, lane, out, out_f64);
 }
 
 }  // namespace tf
