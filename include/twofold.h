@@ -18,8 +18,9 @@
  *   TF_KAHAN     Kahan's compensated summation (Example 2): the pair is the
  *                sum and the compensation not yet applied (-c); dots use
  *                the rounded product, as the paper's dotk
- * Dot products take x[i]*y[i] in place of data[i] (end of the Algorithms
- * section); the twofold variants also add each product's exact rounding
+ * Dot products feed the product x[i]*y[i] as the item (the paper's remark at
+ * the end of the Algorithms section); the twofold variants also add each
+ * product's exact rounding
  * error, from TwoProduct p = RN(x*y), ep = fma(x, y, -p), to the error term.
  * TF_WIDE forms the product exactly in its accumulator format.
  *
@@ -114,8 +115,8 @@ tf_status tf_sum(const void* x, int64_t n, tf_dtype dtype, tf_variant variant,
                  void* out, void* ws, size_t ws_bytes, uint32_t flags,
                  tf_stream_t stream);
 
-/* Twofold dot product sum x[i]*y[i], i < n (x, y of the same dtype);
-   "multiplication like a[i]*b[i] in place of data[i]" plus TwoProduct. */
+/* Twofold dot product sum x[i]*y[i], i < n (x, y of the same dtype): the
+   summation loops with the product as the item, plus TwoProduct. */
 tf_status tf_dot(const void* x, const void* y, int64_t n, tf_dtype dtype,
                  tf_variant variant, void* out, void* ws, size_t ws_bytes,
                  uint32_t flags, tf_stream_t stream);

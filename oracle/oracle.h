@@ -13,8 +13,8 @@
  *      with the exact product formed in integer arithmetic).
  *   2. The paper's sequential loops: sum, sumd, sumk, sumtf, sumt (Examples
  *      1-3 and the double-accumulator listing in section "Algorithms") and the
- *      dot-product forms ("multiplication like a[i]*b[i] in place of
- *      data[i]"), plus the TwoProduct dot forms.
+ *      dot-product forms (the product of the i-th elements as the item),
+ *      plus the TwoProduct dot forms.
  *   3. An exact fixed-point superaccumulator: the plain definition S = sum x_i
  *      (or sum x_i*y_i with unrounded products) as an exact real, rounded once.
  *   4. An order replay ("emulator") of the kernels' documented reduction order,

@@ -156,12 +156,11 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
     case 3:  /* wide: binary64 accumulator */
         st->s = st->s + y;
         break;
-    case 1: { /* fast, Example 1 */
-        double t = ADD(f, st->s, y);
-        double c = SUB(f, SUB(f, t, st->s), y);
-        if (P->op == 0) st->e = SUB(f, st->e, c);
-        else            st->e = ADD(f, st->e, SUB(f, ep, c));
-        st->s = t;
+    case 1: { /* fast, Example 1: Dekker's correction c of s + y, subtracted from e */
+        const double x = ADD(f, st->s, y);
+        const double c = SUB(f, SUB(f, x, st->s), y);
+        st->e = (P->op == 0) ? SUB(f, st->e, c) : ADD(f, st->e, SUB(f, ep, c));
+        st->s = x;
         break; }
     case 4: { /* kahan, Example 2 with e = -c */
         double yk = ADD(f, y, st->e);
@@ -169,15 +168,12 @@ static inline void feed(const prob_t* P, pr_t* st, int64_t i) {
         st->e = SUB(f, yk, SUB(f, t, st->s));
         st->s = t;
         break; }
-    case 2: { /* rigorous, Example 3 */
-        double t = ADD(f, st->s, y);
-        double yt = SUB(f, t, st->s);
-        double dy = SUB(f, y, yt);
-        double ds = SUB(f, st->s, SUB(f, t, yt));
-        double q = ADD(f, ds, dy);
-        if (P->op == 0) st->e = ADD(f, st->e, q);
-        else            st->e = ADD(f, st->e, ADD(f, q, ep));
-        st->s = t;
+    case 2: { /* rigorous, Example 3: TWO-SUM(s, y) (Theorem 2), error q to e */
+        const double x = ADD(f, st->s, y);
+        const double bv = SUB(f, x, st->s), av = SUB(f, x, bv);
+        const double q = ADD(f, SUB(f, st->s, av), SUB(f, y, bv));
+        st->e = (P->op == 0) ? ADD(f, st->e, q) : ADD(f, st->e, ADD(f, q, ep));
+        st->s = x;
         break; }
     }
 }

@@ -599,11 +599,9 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
             if constexpr (TPROD) e = add_rn(e, sub_rn(ep, c)); else e = sub_rn(e, c);
             s = t;
         } else {
-            T t = add_rn(s, p);
-            T yt = sub_rn(t, s);
-            T dy = sub_rn(p, yt);
-            T ds = sub_rn(s, sub_rn(t, yt));
-            T q = add_rn(ds, dy);
+            // Example 3: TWO-SUM (Theorem 2) of s and the item, its error to e
+            T t, q;
+            two_sum(s, p, t, q);
             if constexpr (TPROD) e = add_rn(e, add_rn(q, ep)); else e = add_rn(e, q);
             s = t;
         }

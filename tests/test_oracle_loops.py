@@ -2,9 +2,9 @@
 
 * The "100 hours" worked example (section Accuracy, second Table 2) with the
   paper's printed results, from ``tests/golden/hundred_hours.txt``.
-* The paper's statement that twofold fast summation computes the value
-  exactly as direct summation does (after Example 2): value bits of sumtf,
-  sumt (and the dot forms) equal those of sum.
+* The paper's remark after Example 2 that the twofold loops leave the value
+  itself as direct summation computes it: value bits of sumtf, sumt (and the
+  dot forms) equal those of sum.
 * Theorem 2 on two items: sumt of (a, b) is TWO-SUM(a, b).
 * Special cases: integer data, where every operation is exact.
 * The known error bound of the rigorous (TWO-SUM based) compensated sum,
