@@ -155,15 +155,18 @@ def workspace_size(op="sum", batched=False, dtype=torch.float32, variant="fast",
 
 
 def workspace(nbytes, device=None):
-    """A zero-filled uint8 workspace of at least nbytes on `device`, cached and
-    grown on demand (allocated by torch, never by the library)."""
+    """A zero-filled uint8 workspace of at least nbytes on `device`, cached per
+    (device, current stream) and grown on demand (allocated by torch, never by
+    the library).  Calls in flight on different streams thus never share one:
+    a workspace holds the per-call tickets and block pairs."""
     dev = torch.device(device if device is not None else "cuda")
     if dev.index is None:
         dev = torch.device("cuda", torch.cuda.current_device())
-    ws = _ws_cache.get(dev)
+    key = (dev, torch.cuda.current_stream(dev).cuda_stream)
+    ws = _ws_cache.get(key)
     if ws is None or ws.numel() < nbytes:
         ws = torch.zeros(max(nbytes, 1 << 16), dtype=torch.uint8, device=dev)
-        _ws_cache[dev] = ws
+        _ws_cache[key] = ws
     return ws
 
 

@@ -545,6 +545,30 @@ def test_csr_no_segments():
 
 
 # ------------------------------------------------ reproducibility, graphs
+def test_concurrent_streams_default_workspaces():
+    """Calls in flight on different streams without an explicit workspace get
+    one each (a workspace holds the per-call tickets); eight reductions on
+    four streams, issued without waiting, match the same calls run one by one."""
+    n = (1 << 22) + 5
+    xs = [I.normal(n, "f32", seed=30 + k, device=DEV) for k in range(8)]
+    want = [_np(tf.sum(x, "rigorous")).copy() for x in xs]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    outs = []
+    torch.cuda.synchronize()
+    for k, x in enumerate(xs):
+        st = streams[k % 4]
+        with torch.cuda.stream(st):
+            outs.append(tf.sum(x, "rigorous"))
+    torch.cuda.synchronize()
+    for o, w in zip(outs, want):
+        assert same_bits(_np(o), w)
+    wss = set()
+    for st in streams:
+        with torch.cuda.stream(st):
+            wss.add(tf.workspace(0, DEV).data_ptr())
+    assert len(wss) == 4
+
+
 def test_bit_reproducible_runs_streams_and_graph():
     n = (1 << 22) + 7
     x = I.normal(n, "f32", seed=11, device=DEV)
