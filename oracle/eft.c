@@ -15,32 +15,15 @@
 #include <math.h>
 #include <string.h>
 
-#define DEF_FAST_TWO_SUM(T, SUF)                                             \
+#define DEF_SUM_ARRAYS(T, SUF)                                               \
 void orc_fast_two_sum_##SUF(const T* a, const T* b, int64_t n, T* x, T* y) { \
-    for (int64_t i = 0; i < n; ++i) {                                        \
-        T xi = a[i] + b[i];      /* x  <- a (+) b  */                        \
-        T bv = xi - a[i];        /* b' <- x (-) a  */                        \
-        T yi = b[i] - bv;        /* y  <- b (-) b' */                        \
-        x[i] = xi; y[i] = yi;                                                \
-    }                                                                        \
-}
-DEF_FAST_TWO_SUM(float, f32)
-DEF_FAST_TWO_SUM(double, f64)
-
-#define DEF_TWO_SUM(T, SUF)                                                  \
+    for (int64_t i = 0; i < n; ++i) orc_fts_##SUF(a[i], b[i], &x[i], &y[i]); \
+}                                                                            \
 void orc_two_sum_##SUF(const T* a, const T* b, int64_t n, T* x, T* y) {      \
-    for (int64_t i = 0; i < n; ++i) {                                        \
-        T xi = a[i] + b[i];      /* 1. x  <- a (+) b   */                    \
-        T bv = xi - a[i];        /* 2. b' <- x (-) a   */                    \
-        T av = xi - bv;          /* 3. a' <- x (-) b'  */                    \
-        T bs = b[i] - bv;        /* 4. b# <- b (-) b'  */                    \
-        T as = a[i] - av;        /* 5. a# <- a (-) a'  */                    \
-        T yi = as + bs;          /* 6. y  <- a# (+) b# */                    \
-        x[i] = xi; y[i] = yi;                                                \
-    }                                                                        \
+    for (int64_t i = 0; i < n; ++i) orc_ts_##SUF(a[i], b[i], &x[i], &y[i]);  \
 }
-DEF_TWO_SUM(float, f32)
-DEF_TWO_SUM(double, f64)
+DEF_SUM_ARRAYS(float, f32)
+DEF_SUM_ARRAYS(double, f64)
 
 /* ---- TwoProduct from the definition --------------------------------- */
 

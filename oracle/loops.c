@@ -36,13 +36,13 @@
 #define DEF_STEPS(T, SUF)                                                     \
 static inline void fast_item_##SUF(T* s, T* e, T y, T ep, int with_ep) {      \
     T t, term;                                                                \
-    orc_fast_two_sum_##SUF(s, &y, 1, &t, &term);                              \
+    orc_fts_##SUF(*s, y, &t, &term);                                          \
     *e = with_ep ? *e + (ep + term) : *e + term;                              \
     *s = t;                                                                   \
 }                                                                             \
 static inline void rigorous_item_##SUF(T* s, T* e, T y, T ep, int with_ep) {  \
     T t, term;                                                                \
-    orc_two_sum_##SUF(s, &y, 1, &t, &term);                                   \
+    orc_ts_##SUF(*s, y, &t, &term);                                           \
     *e = with_ep ? *e + (term + ep) : *e + term;                              \
     *s = t;                                                                   \
 }                                                                             \

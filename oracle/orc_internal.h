@@ -33,6 +33,27 @@ static inline void orc_decompose_f64(double a, int* neg, uint64_t* m, int* k, in
     else { *m = f | (1ull << 52); *k = be - 1075; }
 }
 
-
+/* The two sum transforms on one pair, written from the theorems (section
+   "Algorithms"): Dekker's FAST-TWO-SUM (Theorem 1) and Knuth's TWO-SUM
+   (Theorem 2); the exported array forms in eft.c and the sequential loops in
+   loops.c both use them. */
+#define ORC_DEF_SUM_EFTS(T, SUF)                                              \
+static inline void orc_fts_##SUF(T a, T b, T* x, T* y) {                      \
+    const T xi = a + b;                  /* x  <- a (+) b  */                 \
+    const T bv = xi - a;                 /* b' <- x (-) a  */                 \
+    *x = xi;                                                                  \
+    *y = b - bv;                         /* y  <- b (-) b' */                 \
+}                                                                             \
+static inline void orc_ts_##SUF(T a, T b, T* x, T* y) {                       \
+    const T xi = a + b;                  /* 1. x  <- a (+) b   */             \
+    const T bv = xi - a;                 /* 2. b' <- x (-) a   */             \
+    const T av = xi - bv;                /* 3. a' <- x (-) b'  */             \
+    const T bs = b - bv;                 /* 4. b# <- b (-) b'  */             \
+    const T as = a - av;                 /* 5. a# <- a (-) a'  */             \
+    *x = xi;                                                                  \
+    *y = as + bs;                        /* 6. y  <- a# (+) b# */             \
+}
+ORC_DEF_SUM_EFTS(float, f32)
+ORC_DEF_SUM_EFTS(double, f64)
 
 #endif
