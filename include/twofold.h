@@ -40,8 +40,10 @@
  *   batched: the concatenated vector is cut into tiles of plan.tile elements;
  *   in a segment's piece of a tile, element at tile offset r goes to lane
  *   (r/V) mod 32, chain ((r/V)/32 mod U)*V + r mod V; lanes fold as above;
- *   a segment spanning k tiles merges its k piece pairs by 32 lanes (lane l
- *   takes pieces l, l+32, ...) and the butterfly.
+ *   a segment spanning k <= 32 tiles merges its k piece pairs as 32 lanes
+ *   (lane l holds piece l, +0 pairs after k) and the butterfly; beyond 32 by
+ *   a pairwise tree in tile order (the pair of piece j, j a multiple of 2w,
+ *   takes the pair of piece j + w for w = 1, 2, 4, ... while j + w < k).
  * For binary32 data the cross-block (and cross-tile) merge of the twofold and
  * wide variants runs in binary64 and the output is v = RN32(V),
  * e = RN32((V - v) + E) from the binary64 pair (V, E); the plain variant stays
