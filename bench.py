@@ -36,6 +36,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from fractions import Fraction
 
@@ -150,7 +151,9 @@ class ClockSampler:
         self.index = index
         self.enabled = enabled
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        # the raw samples; TF_BENCH_CLOCKS_DIR keeps them somewhere lasting
+        base = os.environ.get("TF_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(base, "bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         if not self.enabled:

@@ -9,7 +9,7 @@ torch arithmetic, so the same code fills host or device memory; the float
 conversions from those words are exact.  Distributions that need
 transcendental functions (normal, log-normal, log-uniform lengths) may differ
 in the last bits between devices, so tests hand the generated array itself to
-the CPU checker.
+the oracle.
 
 The workloads follow the paper's and the benchmark's shapes: uniform data on
 [-1, 1) (the paper's accuracy table), N(0,1) and signed log-normal(0, 2)
