@@ -170,6 +170,13 @@ def workspace(nbytes, device=None):
     return ws
 
 
+def workspace_reset(ws):
+    """Zero-fill a workspace on the current stream (tf_workspace_reset): the
+    state a workspace needs before its first use."""
+    _check("tf_workspace_reset", lib().tf_workspace_reset(_ptr(ws), ws.numel(), _stream(ws)))
+    return ws
+
+
 # ------------------------------------------------------------ reductions
 def _out(x, n_pairs, out_f64, out):
     odt = torch.float64 if (x.dtype == torch.float64 or out_f64) else x.dtype

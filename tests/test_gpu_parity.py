@@ -516,6 +516,30 @@ def test_csr_staged_ring_edges(dt, unroll, block):
                             before["blocks_per_sm"], before["tile"])
 
 
+def test_workspace_reset_restores_a_scribbled_workspace():
+    """A workspace filled with garbage (tickets, counters, flags) is zeroed by
+    tf_workspace_reset, after which flat and batched calls on it give the
+    replay's bits and no device error."""
+    n = 300001
+    x = I.normal(n, "f32", seed=44, device=DEV)
+    off_h = make_csr(40, 1, 30000, seed=45)
+    xs = I.normal(int(off_h[-1]), "f32", seed=46, device=DEV)
+    nb = max(tf.workspace_size("sum", False, torch.float32, "rigorous", n),
+             tf.workspace_size("sum", True, torch.float32, "rigorous", xs.numel(), 40))
+    ws = torch.full((nb,), 0x5A, dtype=torch.uint8, device=DEV)
+    tf.workspace_reset(ws)
+    assert int(ws.max().item()) == 0
+    got = _np(tf.sum(x, "rigorous", ws=ws))
+    block, unroll, grid, _ = tf.launch_shape("sum", False, torch.float32, "rigorous", n)
+    assert same_bits(got, O.replay_flat("sum", "rigorous", _np(x), block=block, unroll=unroll,
+                                        grid=grid))
+    off = torch.from_numpy(off_h).to(DEV)
+    got = _np(tf.sum_batched(xs, off, "rigorous", ws=ws))
+    _, unroll, _, tile = tf.launch_shape("sum", True, torch.float32, "rigorous", xs.numel())
+    assert same_bits(got, O.replay_csr("sum", "rigorous", _np(xs), off_h, unroll=unroll, tile=tile))
+    assert tf.device_error(ws) == 0
+
+
 def test_csr_invalid_offsets_flagged_then_recovers():
     x = I.uniform(1000, "f32", seed=1, device=DEV)
     ws = tf.workspace(tf.workspace_size("sum", True, torch.float32, "fast", 1000, 4), DEV)
