@@ -22,7 +22,7 @@ constexpr size_t kStageOffset = 16;     // WsHeader::stage
 
 std::mutex g_mu;
 
-struct DevInfo { int sms = 0; int ok = -1; };
+struct DevInfo { int sms = 0; int smem_sm = 0; int ok = -1; };
 DevInfo g_dev[64];
 
 constexpr int kVariants = 5;          // plain, fast, rigorous, wide, kahan
@@ -59,25 +59,39 @@ void init_plans_locked() {
 // the plan class of a single-vector call of n elements
 int flat_class(int64_t n) { return n <= (int64_t)TF_SMALL_N ? TF_PLAN_FLAT_SMALL : TF_PLAN_FLAT; }
 
-tf_status check_device(int* sms) {
+tf_status check_device(int* sms, int* smem_sm = nullptr) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TF_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_mu);
     DevInfo& d = g_dev[dev];
     if (d.ok < 0) {
-        int major = 0, minor = 0, sm = 0;
+        int major = 0, minor = 0, sm = 0, smem = 0;
         if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess) {
             cudaGetLastError();
             return TF_ERR_UNSUPPORTED;
         }
         d.sms = sm;
+        d.smem_sm = smem;
         d.ok = (major == 10 && minor == 3) ? 1 : 0;
     }
     if (!d.ok) return TF_ERR_UNSUPPORTED;
     *sms = d.sms;
+    if (smem_sm) *smem_sm = d.smem_sm;
     return TF_OK;
+}
+
+// The batched kernel stages its input through shared memory only when the
+// plan's blocks_per_sm blocks, each with its ring (and the 1 KiB the runtime
+// keeps per block, plus the kernel's barriers), fit in one SM's shared
+// memory; a plan asking for more resident blocks than the rings allow runs
+// the register-loading kernel at that residency (same bits).
+bool csr_ring_fits(const tf_plan& p, int op, int smem_sm) {
+    const size_t per_block = tf::csr_tma_smem_bytes(op, p.block) + 2048;
+    return (size_t)p.blocks_per_sm * per_block <= (size_t)smem_sm;
 }
 
 bool plan_valid(const tf_plan& p, int cls, int dtype) {
@@ -178,14 +192,15 @@ tf_status run_csr(int op, const void* x, const void* y, int64_t n, const int64_t
     if (ws_bytes < tf::csr_ws_bytes(n, nseg)) return TF_ERR_WORKSPACE;
     if (nseg == 0) return TF_OK;
     if (nseg > (int64_t)1 << 40) return TF_ERR_UNSUPPORTED;
-    int sms = 0;
-    if ((s = check_device(&sms)) != TF_OK) return s;
+    int sms = 0, smem_sm = 0;
+    if ((s = check_device(&sms, &smem_sm)) != TF_OK) return s;
     const tf_plan p = force ? *force : get_plan(op, 1, dtype, variant);
     const int64_t grid = csr_grid(p, sms);
     const int aligned = ((uintptr_t)x % 16 == 0) && (op == 0 || (uintptr_t)y % 16 == 0);
+    const int staged = aligned && csr_ring_fits(p, op, smem_sm);
     cudaError_t e = tf::launch_csr(dtype, kernel_variant(op, variant, flags), op, p.unroll, x, y,
                                    n, off, nseg, out, ws, ws_bytes, p.block, grid, p.tile,
-                                   aligned, (flags & TF_OUT_F64) ? 1 : 0, st);
+                                   aligned, staged, (flags & TF_OUT_F64) ? 1 : 0, st);
     return e == cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
 

@@ -243,7 +243,7 @@ template <typename T, int VAR, bool DOT>
 static cudaError_t launch_u(int unroll, const void* x, const void* y, int64_t n,
                             const int64_t* off, int64_t nseg, void* out, void* ws,
                             size_t ws_bytes, int block, int64_t grid, int64_t tile, int aligned,
-                            int out_f64, cudaStream_t st) {
+                            int staged, int out_f64, cudaStream_t st) {
     (void)ws_bytes;
     unsigned char* w = static_cast<unsigned char*>(ws);
     const size_t cnt_bytes = csr_cnt_bytes(n);
@@ -254,7 +254,7 @@ static cudaError_t launch_u(int unroll, const void* x, const void* y, int64_t n,
     csr_prepare<T, VAR><<<pblocks, 256, 0, st>>>(off, nseg, n, tile, out, w, tile_seg, out_f64);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    if (aligned && csr_tma_usable(sizeof(T) == 4 ? 0 : 1, DOT ? 1 : 0, block, tile))
+    if (aligned && staged && csr_tma_usable(sizeof(T) == 4 ? 0 : 1, DOT ? 1 : 0, block, tile))
         return launch_csr_tma(sizeof(T) == 4 ? 0 : 1, VAR, DOT ? 1 : 0, unroll, x, y, off, nseg, out,
                               w, cnt_bytes, tile_seg, block, grid, tile, out_f64, st);
     const T* xp = static_cast<const T*>(x);
@@ -272,34 +272,34 @@ template <typename T, int VAR>
 static cudaError_t launch_d(int dot, int unroll, const void* x, const void* y, int64_t n,
                             const int64_t* off, int64_t nseg, void* out, void* ws,
                             size_t ws_bytes, int block, int64_t grid, int64_t tile, int aligned,
-                            int out_f64, cudaStream_t st) {
-    return dot ? launch_u<T, VAR, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st)
-               : launch_u<T, VAR, false>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
+                            int staged, int out_f64, cudaStream_t st) {
+    return dot ? launch_u<T, VAR, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st)
+               : launch_u<T, VAR, false>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
 }
 
 cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* x,
                        const void* y, int64_t n, const int64_t* off, int64_t nseg,
                        void* out, void* ws, size_t ws_bytes, int block, int64_t grid,
-                       int64_t tile, int aligned, int out_f64, cudaStream_t st) {
+                       int64_t tile, int aligned, int staged, int out_f64, cudaStream_t st) {
     if (dtype == 0) {
         switch (variant) {
-        case PLAIN: return launch_d<float, PLAIN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case FAST: return launch_d<float, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case RIGOROUS: return launch_d<float, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case WIDE: return launch_d<float, WIDE>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case KAHAN: return launch_d<float, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case FAST_LIT: return dot ? launch_u<float, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
-        case RIG_LIT: return dot ? launch_u<float, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
+        case PLAIN: return launch_d<float, PLAIN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case FAST: return launch_d<float, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case RIGOROUS: return launch_d<float, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case WIDE: return launch_d<float, WIDE>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case KAHAN: return launch_d<float, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case FAST_LIT: return dot ? launch_u<float, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st) : cudaErrorInvalidValue;
+        case RIG_LIT: return dot ? launch_u<float, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st) : cudaErrorInvalidValue;
         }
     } else {
         switch (variant) {
-        case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case WIDE: return launch_d<double, WIDE>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case KAHAN: return launch_d<double, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st);
-        case FAST_LIT: return dot ? launch_u<double, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
-        case RIG_LIT: return dot ? launch_u<double, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, out_f64, st) : cudaErrorInvalidValue;
+        case PLAIN: return launch_d<double, PLAIN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case FAST: return launch_d<double, FAST>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case RIGOROUS: return launch_d<double, RIGOROUS>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case WIDE: return launch_d<double, WIDE>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case KAHAN: return launch_d<double, KAHAN>(dot, unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st);
+        case FAST_LIT: return dot ? launch_u<double, FAST_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st) : cudaErrorInvalidValue;
+        case RIG_LIT: return dot ? launch_u<double, RIG_LIT, true>(unroll, x, y, n, off, nseg, out, ws, ws_bytes, block, grid, tile, aligned, staged, out_f64, st) : cudaErrorInvalidValue;
         }
     }
     return cudaErrorInvalidValue;

@@ -18,11 +18,13 @@ cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void*
                         const void* y, int64_t n, void* out, void* ws, int block,
                         int64_t grid, int aligned, int out_f64, cudaStream_t st);
 
-// batched reduction: the offsets check, then the persistent kernel
+// batched reduction: the offsets check, then the persistent kernel (the
+// shared-memory ring one when `staged` and the plan fits its ring, else the
+// register-loading one)
 cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* x,
                        const void* y, int64_t n, const int64_t* off, int64_t nseg,
                        void* out, void* ws, size_t ws_bytes, int block, int64_t grid,
-                       int64_t tile, int aligned, int out_f64, cudaStream_t st);
+                       int64_t tile, int aligned, int staged, int out_f64, cudaStream_t st);
 size_t csr_ws_bytes(int64_t n, int64_t nseg);
 // the batched kernel staged through shared memory by bulk copies (16-byte
 // aligned inputs; plans whose tile and block fit its ring)

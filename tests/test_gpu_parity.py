@@ -472,9 +472,12 @@ def test_csr_bit_exact_vs_replay(dt, op, variant):
             assert abs(ex[s]["r"]) <= twofold_bound(ex[s]["s"], ex[s]["sabs"], u, 2 * D)
 
 
+@pytest.mark.parametrize("bps", [1, 4])
 @pytest.mark.parametrize("tile", [1024, 4096, 16384])
-def test_csr_tiles_and_long_segments(tile):
-    # one segment over many tiles, many tiny ones, and segments ending on tile edges
+def test_csr_tiles_and_long_segments(tile, bps):
+    # one segment over many tiles, many tiny ones, and segments ending on tile
+    # edges; one block per SM stages through the shared-memory ring (tiles of
+    # 4096 and more), four per SM leave no room for it and load into registers
     L = [tile * 40 + 17, 1, 2, 3, tile - 6, tile, 0, 2 * tile, 5, 100000, 0, 0, 31]
     off_h = I.csr_offsets(L)
     n = int(off_h[-1])
@@ -484,7 +487,7 @@ def test_csr_tiles_and_long_segments(tile):
         for op, variant in (("sum", "rigorous"), ("dot", "fast"), ("sum", "plain")):
             before = tf.plan_get(op, True, TD[dt], variant)
             try:
-                tf.plan_set(op, True, TD[dt], variant, 256, 2, 4, tile)
+                tf.plan_set(op, True, TD[dt], variant, 256, 2, bps, tile)
                 check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
             finally:
                 tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
@@ -495,9 +498,10 @@ def test_csr_tiles_and_long_segments(tile):
 @pytest.mark.parametrize("unroll,block", [(1, 128), (2, 512), (4, 256)])
 def test_csr_staged_ring_edges(dt, unroll, block):
     """The shared-memory ring of the batched kernel (16-byte-aligned inputs,
-    tile 4096): totals that end inside a 16-byte vector (the tail is read from
-    global memory), totals below one vector, empty segments, pieces that start
-    and end inside a chunk, and runs of tiles past the ring's depth."""
+    tile 4096, one block per SM so that the ring fits): totals that end inside
+    a 16-byte vector (the tail is read from global memory), totals below one
+    vector, empty segments, pieces that start and end inside a chunk, and runs
+    of tiles past the ring's depth."""
     tile = 4096
     cases = [[1], [3], [0, 5, 0], [tile * 3 + 3], [2, tile - 1, 7, tile * 2 + 1, 0, 9],
              [tile * 9 + 1, 1, 1], [17] * 700]
@@ -509,7 +513,7 @@ def test_csr_staged_ring_edges(dt, unroll, block):
         for op, variant in (("sum", "rigorous"), ("dot", "fast"), ("sum", "kahan")):
             before = tf.plan_get(op, True, TD[dt], variant)
             try:
-                tf.plan_set(op, True, TD[dt], variant, block, unroll, 2, tile)
+                tf.plan_set(op, True, TD[dt], variant, block, unroll, 1, tile)
                 check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
             finally:
                 tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
