@@ -143,6 +143,10 @@ def test_c3_f32_dot_n2p30_precision_form(dist):
     assert abs(ex.r) <= twofold_bound(ex.s, ex.sabs, U32, D)
     S = Fraction(ex.s) + Fraction(ex.s_lo)
     rt = rel(S, tw[0], tw[1])
+    # reported with -s: relative errors of each form against the exact dot
+    print("\nC3 %s: cond %.3g  rigorous v+e %.3g  v %.3g  fast v+e %.3g  wide %.3g  plain %.3g"
+          % (dist, ex.sabs / abs(ex.s), rt, rel(S, tw[0]), rel(S, fa[0], fa[1]), rel(S, wide[0]),
+             rel(S, plain[0])))
     # FP32-arithmetic twofold against binary64 accumulation and plain binary32
     assert rt <= rel(S, plain[0])
     assert rel(S, fa[0], fa[1]) <= rel(S, plain[0])
@@ -201,6 +205,13 @@ def test_c5_f64_dot_n2p29_cond_sweep_tracking_and_reproducible():
         assert err <= twofold_bound(float(S), ic.sum_abs, U64, D), cond
         # the error term estimates value - exact while gamma_D^2 * cond << 1
         rv = S - Fraction(float(rig[0]))
+        rvf = S - Fraction(float(fast[0]))
+        print("\nC5 cond %.0e: rigorous |v+e-S|/|S| %.3g, |v-S|/|S| %.3g, e/(S-v) %s; "
+              "fast |v+e-S|/|S| %.3g, e/(S-v) %s"
+              % (cond, err / abs(float(S)), abs(float(rv)) / abs(float(S)),
+                 "%.6f" % float(Fraction(float(rig[1])) / rv) if rv != 0 else "v exact",
+                 float(abs(S - Fraction(float(fast[0])) - Fraction(float(fast[1])))) / abs(float(S)),
+                 "%.6f" % float(Fraction(float(fast[1])) / rvf) if rvf != 0 else "v exact"))
         if rv != 0 and (D * U64) ** 2 * cond < 0.1:
             rho = float(Fraction(float(rig[1])) / rv)
             assert 0.5 <= rho <= 2.0, (cond, rho)
