@@ -103,7 +103,10 @@ typedef struct {
     int32_t block;           /* threads per block: 128, 256 or 512                */
     int32_t unroll;          /* 128-bit loads per thread per step U: 1, 2 or 4;
                                 a thread runs U * (16 / sizeof(element)) chains    */
-    int32_t blocks_per_sm;   /* grid = blocks_per_sm * SM count (1..8)            */
+    int32_t blocks_per_sm;   /* grid = blocks_per_sm * SM count (1..8); batched:
+                                16-byte-aligned inputs stream through a shared-
+                                memory ring when that many blocks' rings fit an
+                                SM, else through registers (same bits)         */
     int32_t tile;            /* batched only: elements per warp tile, a multiple
                                 of 32 * 16 / sizeof(element) (e.g. 4096); 0 flat  */
 } tf_plan;
