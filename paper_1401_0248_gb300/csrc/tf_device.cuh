@@ -307,34 +307,43 @@ static __device__ __noinline__ double2 two_product_slow(double a, double b) {
 // underflows are excluded).  Returns false, leaving p and e untouched, for
 // zero, subnormal or non-finite operands and for exponent sums where p or e
 // would leave the normal range; callers then use the FMA form.  Same bits.
+// A product below 2^105 is doubled first (a multiply by 2, on the FMA pipe),
+// so the rounding point is always bit 53 and every shift is a constant one.
 __device__ __forceinline__ bool two_product_i64(double a, double b, double& p, double& e) {
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
     const unsigned long long B = (unsigned long long)__double_as_longlong(b);
     const unsigned long long M52 = 0x000fffffffffffffull;
     const int ea = (int)((A >> 52) & 0x7ff), eb = (int)((B >> 52) & 0x7ff);
     const int es = ea + eb;
-    if (ea == 0 || eb == 0 || ea == 2047 || eb == 2047 || es < 1128 || es > 3067) return false;
+    // ea, eb in [1, 2046] (normal, finite) and es in [1128, 3067]
+    if ((unsigned)(ea - 1) >= 2046u || (unsigned)(eb - 1) >= 2046u || (unsigned)(es - 1128) > 1939u)
+        return false;
     const unsigned long long ma = (A & M52) | (1ull << 52);
     const unsigned long long mb = (B & M52) | (1ull << 52);
-    const unsigned long long lo = ma * mb;
-    const unsigned long long hi = __umul64hi(ma, mb);          // product in [2^104, 2^106)
-    const int sh = ((hi >> 41) & 1ull) ? 53 : 52;
-    unsigned long long q = (hi << (64 - sh)) | (lo >> sh);
-    const unsigned long long rem = lo & ((1ull << sh) - 1ull);
-    const unsigned long long half = 1ull << (sh - 1);
+    unsigned long long lo = ma * mb;
+    unsigned long long hi = __umul64hi(ma, mb);          // product in [2^104, 2^106)
+    const unsigned int top = (unsigned int)(hi >> 41) & 1u;   // product >= 2^105
+    const unsigned int m = 2u - top;
+    hi = hi * m + ((lo >> 63) & (unsigned long long)(1u - top));
+    lo = lo * m;                                           // now in [2^105, 2^106)
+    unsigned long long q = (hi << 11) | (lo >> 53);
+    const unsigned long long rem = lo & ((1ull << 53) - 1ull);
+    const unsigned long long half = 1ull << 52;
     const bool up = rem > half || (rem == half && (q & 1ull));
-    const unsigned long long rmag = up ? ((1ull << sh) - rem) : rem;
+    const unsigned long long rmag = up ? ((1ull << 53) - rem) : rem;
     q += up ? 1ull : 0ull;
-    int ex = es + sh - 1075;
+    int ex = es - 1023 + (int)top;
     if (q == (1ull << 53)) { q >>= 1; ex += 1; }
     const unsigned long long sg = (A ^ B) >> 63;
     p = __longlong_as_double((long long)((sg << 63) | ((unsigned long long)ex << 52) | (q & M52)));
     if (rmag == 0ull) {
         e = 0.0;
     } else {
+        // rmag counts units of 2^(es - 2151 + top)
         const int pr = 63 - __clzll((long long)rmag);          // <= 52
         const unsigned long long se = sg ^ (up ? 1ull : 0ull);
-        e = __longlong_as_double((long long)((se << 63) | ((unsigned long long)(es + pr - 1127) << 52) |
+        e = __longlong_as_double((long long)((se << 63) |
+                                             ((unsigned long long)(es + pr - 1128 + (int)top) << 52) |
                                              ((rmag << (52 - pr)) & M52)));
     }
     return true;
