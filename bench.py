@@ -771,6 +771,79 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_layouts(args):
+    """Batched binary32 fast sum and dot on layouts that separate the costs
+    of the batched kernel: one segment per tile, two per tile, segments of two
+    tiles, segments offset by half a tile (two cross-tile pieces per tile),
+    one segment, and the 16,384-segment configuration, beside the flat kernel
+    on the same elements (tile 16,384, CUDA-graph replay, inputs > L2)."""
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    from paper_1401_0248_gb300 import twofold as tf
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev)
+    T, ntile = 16384, 26607
+    n = T * ntile
+    Lc4 = I.csr_lengths(16384, 16, 1 << 18, seed=0)
+    nal = max(n, int(I.csr_offsets(Lc4)[-1]))
+    xa = I.uniform(nal, "f32", seed=1, device=dev)
+    ya = I.uniform(nal, "f32", seed=1, stream=1, device=dev)
+    layouts = {"one_seg_per_tile": [T] * ntile, "two_segs_per_tile": [T // 2] * (2 * ntile),
+               "segs_of_two_tiles": [2 * T] * (ntile // 2) + [T] * (ntile % 2),
+               "segs_offset_half_tile": [T // 2] + [T] * (ntile - 1) + [T // 2],
+               "one_segment": [n], "c4_16384_segments": list(Lc4)}
+
+    def timed(call):
+        call()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream(device=dev)
+        gs.wait_stream(st)
+        with torch.cuda.stream(gs):
+            with torch.cuda.graph(g, stream=gs):
+                call()
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            g.replay()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(args.steps):
+            g.replay()
+        b.record(st)
+        torch.cuda.synchronize()
+        return round(a.elapsed_time(b) / args.steps, 4)
+
+    res = {"tile": T, "elements": n, "ms": {}}
+    for op in ("sum", "dot"):
+        x, y = xa[:n], ya[:n]
+        ws = torch.zeros(tf.workspace_size(op, False, torch.float32, "fast", n), dtype=torch.uint8,
+                         device=dev)
+        out = torch.empty(2, device=dev)
+        res["ms"]["flat_%s" % op] = timed(
+            (lambda: tf.sum(x, "fast", ws=ws, out=out)) if op == "sum" else
+            (lambda: tf.dot(x, y, "fast", ws=ws, out=out)))
+        p = tf.plan_get(op, True, torch.float32, "fast")
+        tf.plan_set(op, True, torch.float32, "fast", p["block"], p["unroll"], p["blocks_per_sm"], T)
+        try:
+            for name, L in layouts.items():
+                oh = I.csr_offsets(L)
+                m = int(oh[-1])
+                xs, ys = xa[:m], ya[:m]
+                off = torch.from_numpy(oh).to(dev)
+                wsb = torch.zeros(tf.workspace_size(op, True, torch.float32, "fast", m, len(L)),
+                                  dtype=torch.uint8, device=dev)
+                outb = torch.empty(len(L), 2, device=dev)
+                res["ms"]["%s_%s" % (name, op)] = timed(
+                    (lambda: tf.sum_batched(xs, off, "fast", ws=wsb, out=outb)) if op == "sum" else
+                    (lambda: tf.dot_batched(xs, ys, off, "fast", ws=wsb, out=outb)))
+        finally:
+            tf.plan_set(op, True, torch.float32, "fast", p["block"], p["unroll"],
+                        p["blocks_per_sm"], p["tile"])
+    return res
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -786,11 +859,16 @@ def main(argv=None):
     ap.add_argument("--no-clocks", action="store_true", help="profiling: no nvidia-smi sampler")
     ap.add_argument("--only", default="", help="profiling: comma list of kernels, e.g. f64_dot_rigorous")
     ap.add_argument("--conds", default="1e4,1e8,1e16", help="profiling: condition numbers")
+    ap.add_argument("--layouts", action="store_true",
+                    help="only the batched layout sweep (one JSON line of its own)")
     args = ap.parse_args(argv)
     args.only = set(k for k in args.only.split(",") if k)
     args.conds = tuple(float(c) for c in args.conds.split(","))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.layouts:
+        print(json.dumps({"batched_layouts": run_layouts(args)}))
+        return 0
     rank, world, local = dist_setup()
     if args.impl == "reference":
         res = run_reference(args, rank, world)
