@@ -38,6 +38,8 @@ def plan_class(n, batched=False):
     if batched:
         return PLAN_BATCHED
     return PLAN_FLAT_SMALL if n <= SMALL_N else PLAN_FLAT
+
+
 STATUS = {0: "TF_OK", 1: "TF_ERR_ARG", 2: "TF_ERR_DTYPE", 3: "TF_ERR_WORKSPACE",
           4: "TF_ERR_ALIGN", 5: "TF_ERR_CUDA", 6: "TF_ERR_OFFSETS", 7: "TF_ERR_TIMEOUT",
           8: "TF_ERR_UNSUPPORTED"}
@@ -110,7 +112,7 @@ def lib():
                 if plans != "none" and os.path.exists(plans):
                     rc = L.tf_plan_load(os.fsencode(plans))
                     if rc != 0:
-                        raise TwofoldError("tf_plan_load(%s): %s" % (plans, STATUS.get(rc, rc)))
+                        raise TwofoldError("tf_plan_load(%s)" % plans, rc)
                 _lib = L
     return _lib
 
@@ -243,8 +245,8 @@ def sum_batched(x, offsets, variant="fast", *, out_f64=False, out=None, ws=None)
 def dot_batched(x, y, offsets, variant="fast", *, out_f64=False, out=None, ws=None, literal=False):
     """One twofold dot product per CSR segment: (nseg, 2)."""
     x, y = _flat(x), _flat(y)
-    if x.dtype != y.dtype or x.numel() != y.numel():
-        raise ValueError("twofold.dot_batched: x and y must match in dtype and length")
+    if x.dtype != y.dtype or x.numel() != y.numel() or x.device != y.device:
+        raise ValueError("twofold.dot_batched: x and y must match in dtype, length and device")
     offsets = _offsets(offsets, x)
     nseg = offsets.numel() - 1
     out = _out(x, nseg, out_f64, out)

@@ -95,6 +95,22 @@ def test_plan_save_load_roundtrip(tmp_path):
     assert twofold.plan_class(5, batched=True) == 1
 
 
+def test_bad_default_plan_file_raises(tmp_path):
+    """A plan file named by TF_PLANS that does not parse makes the first use
+    of the library raise TwofoldError (checked in a fresh interpreter)."""
+    import subprocess
+    import sys
+    bad = tmp_path / "bad_plans.txt"
+    bad.write_text("0 0 0 1 100 1 1 0\n")
+    code = ("from paper_1401_0248_gb300 import twofold as t\n"
+            "try:\n    t.lib()\nexcept t.TwofoldError as e:\n    print('raised', e.code)\n")
+    env = dict(os.environ, TF_PLANS=str(bad))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "raised 1" in r.stdout
+
+
 def test_product_path_has_no_cpu_fallback():
     """The binding raises on CPU tensors instead of computing anything."""
     import torch
