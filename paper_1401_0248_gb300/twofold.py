@@ -304,8 +304,9 @@ def sum_host(x, variant="fast", *, out_f64=False, x_dev=None, ws=None, device=No
 
 def dot_host(x, y, variant="fast", *, out_f64=False, x_dev=None, y_dev=None, ws=None, device=None):
     """Twofold dot product of host data (see sum_host)."""
-    if x.is_cuda or y.is_cuda or x.dtype != y.dtype or x.numel() != y.numel():
-        raise ValueError("dot_host: two matching CPU tensors expected")
+    if (x.is_cuda or y.is_cuda or x.dtype != y.dtype or x.numel() != y.numel() or x.dim() != 1
+            or y.dim() != 1 or not x.is_contiguous() or not y.is_contiguous()):
+        raise ValueError("dot_host: two matching 1-D contiguous CPU tensors expected")
     dev = torch.device(device if device is not None else "cuda")
     if x_dev is None:
         x_dev = torch.empty_like(x, device=dev)
