@@ -263,14 +263,21 @@ static tf_status host_call(int op, const void* xh, const void* yh, int64_t n, in
     if (!out_host || (n > 0 && (!xh || !xd || (op == 1 && (!yh || !yd))))) return TF_ERR_ARG;
     if (n < 0) return TF_ERR_ARG;
     if (!ws) return TF_ERR_ARG;
+    void* stage = (char*)ws + kStageOffset;
+    // every argument and the device checked before anything is enqueued
+    tf_status s = common_checks(op, dtype, variant, xd, yd, n, stage, ws, ws_bytes);
+    if (s != TF_OK) return s;
+    if ((flags & TF_OUT_F64) && ((uintptr_t)stage % 8)) return TF_ERR_ALIGN;
+    if (ws_bytes < flat_ws_bytes()) return TF_ERR_WORKSPACE;
+    int sms = 0;
+    if ((s = check_device(&sms)) != TF_OK) return s;
     const size_t bytes = (size_t)n * esize(dtype);
     if (n > 0) {
         if (cudaMemcpyAsync(xd, xh, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return TF_ERR_CUDA;
         if (op == 1 && cudaMemcpyAsync(yd, yh, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return TF_ERR_CUDA;
     }
-    void* stage = (char*)ws + kStageOffset;
-    tf_status s = run_flat(op, xd, yd, n, dtype, variant, stage, ws, ws_bytes, flags, st);
+    s = run_flat(op, xd, yd, n, dtype, variant, stage, ws, ws_bytes, flags, st);
     if (s != TF_OK) return s;
     const size_t ob = (dtype == TF_F64 || (flags & TF_OUT_F64)) ? 16 : 8;
     if (cudaMemcpyAsync(out_host, stage, ob, cudaMemcpyDeviceToHost, st) != cudaSuccess) return TF_ERR_CUDA;

@@ -57,6 +57,12 @@ def test_host_side_checks_without_gpu():
     assert L.tf_sum(None, 10, 7, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 2  # no such dtype
     assert L.tf_sum(C.c_void_p(2), 10, 0, 1, C.c_void_p(256), C.c_void_p(256), 1 << 20, 0, None) == 4
     assert L.tf_sum(C.c_void_p(256), 10, 0, 1, C.c_void_p(256), C.c_void_p(256), 16, 0, None) == 3
+    # host-buffer calls check their arguments before enqueuing any copy
+    res = (C.c_double * 2)()
+    assert L.tf_sum_host(C.c_void_p(16), 10, 0, 9, C.cast(res, C.c_void_p), C.c_void_p(256),
+                         C.c_void_p(256), 1 << 20, 0, None) == 1            # no such variant
+    assert L.tf_dot_host(C.c_void_p(16), C.c_void_p(16), 10, 0, 1, C.cast(res, C.c_void_p),
+                         C.c_void_p(256), C.c_void_p(256), C.c_void_p(256), 16, 0, None) == 3
     p = twofold.Plan(100, 2, 2, 0)
     assert L.tf_plan_set(0, 0, 0, 1, C.byref(p)) == 1          # block must be 128/256/512
     p = twofold.Plan(256, 2, 4, 1000)
