@@ -255,9 +255,11 @@ __device__ __forceinline__ bool fast_two_sum_h64(double a, double b, double& x, 
     if (ea >= eb) { y = err; return true; }
     const unsigned long long E = (unsigned long long)__double_as_longlong(err);
     const unsigned long long M52 = 0x000fffffffffffffull;
-    if ((E << 1) == 0ull) { y = 0.0; return true; }
     const int Eu = eb - 52;                               // exponent field of ulp(b)
     const int eE = (int)((E >> 52) & 0x7ff);
+    // |err| < ulp(b)/4 (err = 0 included: its field is 0 < Eu - 2): b - err
+    // rounds back to b in every case below, so y = 0
+    if (eE < Eu - 2) { y = 0.0; return true; }
     const unsigned long long mE = E & M52, mB = B & M52;
     const unsigned long long sb = B >> 63;
     const bool wpos = ((E >> 63) != sb);                 // b - err moves away from zero
