@@ -110,3 +110,12 @@ def test_reference_arm_json_line_on_cpu():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_bench_refuses_fewer_than_three_warmup_steps():
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--warmup", "2"],
+                       cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "--warmup must be >= 3" in r.stderr
