@@ -165,3 +165,14 @@ def test_exact_batched_equals_per_segment():
 def test_exact_add():
     assert O.exact_add(1.0, 2.0 ** -60) == 1.0
     assert O.exact_add(1.0, 2.0 ** -53, 2.0 ** -105) == 1.0 + 2.0 ** -52
+
+
+def test_ill_conditioned_reaches_its_condition_number():
+    """The generator's achieved cond = sum|x| / |sum x| (from the exact
+    oracle) lies within a factor of 10 of the target, for sums and dots."""
+    for dt, cond in (("f32", 1e4), ("f32", 1e8), ("f64", 1e8), ("f64", 1e16), ("f64", 1e24)):
+        for dot in (False, True):
+            ic = I.ill_conditioned(1 << 16, dt, cond, seed=4, dot=dot)
+            r = O.exact(ic.x.numpy(), ic.y.numpy() if dot else None)
+            got = r.sabs / abs(r.s)
+            assert cond / 10 <= got <= cond * 10, (dt, cond, dot, got)
