@@ -178,3 +178,28 @@ def test_accuracy_table_magnitudes(lo):
     assert 1e-9 < rel_direct < 1e-2
     assert rel_tf < 1e-9
     assert rel_k < 1e-6
+
+
+def test_error_growth_with_n():
+    """Accuracy against N (the paper's closing remarks on how the errors
+    grow): on positive uniform binary32 data the direct sum's relative error
+    grows with N and stays within its gamma_{N-1} bound, while the rigorous
+    twofold pair stays near u^2 N, far below the direct error, for all
+    N < 1/u."""
+    u = 2.0 ** -24
+    prev = 0.0
+    for k in (10, 14, 18, 22):
+        n = 1 << k
+        x = I.uniform(n, "f32", seed=20 + k, lo=0.0).numpy()
+        s, _ = O.loop("sum", x)
+        v, e = O.loop("sumt", x)
+        ex = O.exact(x, v=float(v), e=float(e))
+        S = ex.s
+        rel_direct = abs(float(s) - S) / S
+        rel_twofold = abs(ex.r) / S
+        assert rel_direct <= (n - 1) * u / (1 - (n - 1) * u)
+        assert rel_twofold <= u + 4 * (n * u) ** 2
+        assert rel_twofold < rel_direct * 1e-3 or rel_direct == 0.0
+        if k >= 14:
+            assert rel_direct > prev          # grows with N on this data
+        prev = rel_direct
