@@ -415,6 +415,25 @@ def test_flat_misaligned_pointers_same_bits(dt):
             assert same_bits(a, b)
 
 
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_csr_misaligned_pointers_same_bits(dt):
+    """Batched inputs that are element-aligned but not 16-byte aligned load
+    through registers (no shared-memory ring); the order, hence the bits, is
+    the aligned call's."""
+    off_h = make_csr(300, 1, 20000, seed=47, empties=(5, 6))
+    n = int(off_h[-1])
+    off = torch.from_numpy(off_h).to(DEV)
+    base = I.normal(n + 3, dt, seed=5, device=DEV)
+    ybase = I.normal(n + 3, dt, seed=5, stream=1, device=DEV)
+    for k in (1, 3):
+        x, y = base[k:k + n], ybase[k:k + n]
+        xc, yc = x.clone(), y.clone()
+        for variant in ("fast", "rigorous"):
+            assert same_bits(_np(tf.sum_batched(x, off, variant)), _np(tf.sum_batched(xc, off, variant)))
+            assert same_bits(_np(tf.dot_batched(x, y, off, variant)),
+                             _np(tf.dot_batched(xc, yc, off, variant)))
+
+
 def test_flat_special_values():
     x = torch.tensor([1.0, float("inf"), 2.0], device=DEV)
     out = _np(tf.sum(x, "fast"))
