@@ -20,7 +20,13 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtwofold.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["tf_flat.cu", "tf_csr.cu", "tf_csr_tma.cu", "tf_aux.cu", "tf_api.cu", "tf_noalloc.cu"]
-HEADERS = ["tf_device.cuh", "tf_internal.h"]
+
+
+def _headers():
+    """Every header of csrc/ and include/: a change to any of them rebuilds
+    every object (the translation units include them in different subsets)."""
+    hs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".cuh", ".h"))]
+    return hs + [os.path.join(INCLUDE, f) for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -48,7 +54,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    hdr = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "twofold.h")]
+    hdr = _headers()
     jobs = []
     objs = []
     for src in SOURCES:
