@@ -7,6 +7,11 @@
   dot forms) equal those of sum.
 * Theorem 2 on two items: sumt of (a, b) is TWO-SUM(a, b).
 * Special cases: integer data, where every operation is exact.
+* The literal dot loops (the paper's remark that a dot product runs the
+  summation loop with the product of the i-th elements as the item): each
+  equals its summation loop over the products rounded by numpy's own IEEE
+  multiply, bit for bit; Kahan's dot also obeys the compensated-summation
+  bound against the exact dot.
 * The known error bound of the rigorous (TWO-SUM based) compensated sum,
   |S - (v + e)| <= u|S| + gamma_{n-1}^2 sum|x_i| (Ogita, Rump, Oishi 2005,
   "Accurate sum and dot product", Prop. 4.5 / 5.5), against the exact oracle.
@@ -98,9 +103,47 @@ def test_integer_data_is_exact():
         assert float(v) == S and e == 0
     y = rng.integers(-30, 30, size=10000).astype(np.float32)
     D = float(np.sum(x.astype(np.int64) * y.astype(np.int64)))
-    for m in ("dot", "dottf", "dott", "dottf2", "dott2"):
+    for m in ("dot", "dotk", "dottf", "dott", "dottf2", "dott2"):
         v, e = O.loop(m, x, y)
-        assert float(v) == D and e == 0
+        assert float(v) == D and e == 0, m
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_literal_dots_are_sum_loops_over_rounded_products(dt):
+    """dot, dotk, dottf, dott = sum, sumk, sumtf, sumt of RN(x_i * y_i), the
+    rounding done by numpy (not by the oracle), on inexact products of mixed
+    magnitudes so that every loop's compensation is non-zero."""
+    n = 40001
+    x = I.normal(n, dt, seed=31).numpy()
+    y = I.normal(n, dt, seed=31, stream=2).numpy()
+    y[::3] *= x.dtype.type(1e-3)
+    p = np.multiply(x, y)                 # RN(x_i * y_i) in the data type
+    assert p.dtype == x.dtype
+    for dm, sm in (("dot", "sum"), ("dotk", "sumk"), ("dottf", "sumtf"), ("dott", "sumt")):
+        vd, ed = O.loop(dm, x, y)
+        vs, es = O.loop(sm, p)
+        assert vd.tobytes() == vs.tobytes() and ed.tobytes() == es.tobytes(), dm
+        if dm != "dot":
+            assert ed != 0, dm
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_kahan_dot_bound(dt):
+    """Kahan's dot (Example 2 with the rounded product as the item) against
+    the exact dot: |s - sum x_i y_i| <= u sum|x_i y_i| (the products' own
+    roundings) + (2u + 4 n u^2)(1 + u) sum|x_i y_i| (compensated summation of
+    the rounded products, Goldberg 1991 / Higham 2002 Thm 4.8); the
+    compensated value beats the direct dot on the same data."""
+    n = 100000
+    u = 2.0 ** -24 if dt == "f32" else 2.0 ** -53
+    x = I.uniform(n, dt, seed=32, lo=0.0).numpy()
+    y = I.uniform(n, dt, seed=32, stream=4, lo=0.0).numpy()
+    s, c = O.loop("dotk", x, y)
+    r = O.exact(x, y, v=float(s))
+    assert abs(r.rv) <= (u + (2 * u + 4 * n * u * u) * (1 + u)) * r.sabs
+    d, _ = O.loop("dot", x, y)
+    rd = O.exact(x, y, v=float(d))
+    assert abs(r.rv) < abs(rd.rv)
 
 
 def gamma(k, u):
