@@ -206,7 +206,7 @@ def test_flat_bit_exact_vs_replay(dt, op, variant, n):
         ex = O.exact(_np(x), _np(y) if y is not None else None, v=float(out[0]), e=float(out[1]))
         u = U32 if dt == "f32" else U64
         D = flat_depth(n, 4 if dt == "f32" else 2, block, unroll, grid)
-        assert abs(ex.r) <= twofold_bound(ex.s, ex.sabs, u, 2 * D)
+        assert abs(ex.r) <= twofold_bound(ex.s, ex.sabs, u, D)
 
 
 @pytest.mark.parametrize("dt,cond", [("f64", 1e8), ("f64", 1e16), ("f64", 1e30), ("f32", 1e8)])
@@ -488,7 +488,7 @@ def test_csr_bit_exact_vs_replay(dt, op, variant):
         for s in range(300):
             L = int(off_h[s + 1] - off_h[s])
             D = csr_depth(max(L, 1), 4 if dt == "f32" else 2, unroll, tile)
-            assert abs(ex[s]["r"]) <= twofold_bound(ex[s]["s"], ex[s]["sabs"], u, 2 * D)
+            assert abs(ex[s]["r"]) <= twofold_bound(ex[s]["s"], ex[s]["sabs"], u, D)
 
 
 @pytest.mark.parametrize("bps", [1, 4])
