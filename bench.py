@@ -391,14 +391,14 @@ def run_gpu(args, rank, world, local):
         # bound by the binary64 pipe: its issued adds against the measured rate
         # of the instruction they use (DFMA by 1.0 for sums, DADD for dots)
         fma_adds = op == "sum"
-        peak_ops = (probes or {}).get("dadd_as_fma_reg_gops" if fma_adds else "dadd_gops") \
+        peak_ops = (probes or {}).get("dadd_as_fma_gops" if fma_adds else "dadd_gops") \
             or (FALLBACK_DFMA_GOPS if fma_adds else FALLBACK_DADD_GOPS)
         ops = FP64_PIPE_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": round(ops, 1), "peak": round(peak_ops, 1),
                     "unit": "G binary64-pipe ops/s", "frac": round(ops / peak_ops, 4),
                     "traffic": traffic, "kernel": dom_name,
                     "peak_source": ("measured rate of binary64 adds issued as DFMA by a runtime "
-                                    "1.0 (probe kind 13) on this GPU" if fma_adds else
+                                    "1.0 (probe kind 10) on this GPU" if fma_adds else
                                     "measured binary64 add rate (probe kind 1) on this GPU")
                                    if probes else "fallback (no probes)",
                     "paper_ops_per_s_g": round(PAPER_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9, 1),
@@ -454,9 +454,7 @@ def run_probes(data, dev, stream, cond0):
     blocks, threads = 4 * sms, 256
     for kind, iters in (("fadd", 20000), ("dadd", 2000), ("dfma", 2000), ("iadd", 20000),
                         ("fast_f32", 5000), ("rigorous_f32", 3000), ("fast_f64", 500),
-                        ("rigorous_f64", 300), ("dadd_as_fma", 2000), ("dmul", 2000),
-                        ("cvt_f32_f64", 2000), ("dadd_as_fma_const", 2000),
-                        ("dadd_as_fma_reg", 2000)):
+                        ("rigorous_f64", 300), ("dmul", 2000), ("dadd_as_fma", 2000)):
         tf.probe_alu(kind, iters // 10, blocks, threads, device=dev)
         a = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)

@@ -241,15 +241,15 @@ tf_status tf_count_large_errors(const void* pairs, int64_t npairs, tf_dtype pair
    prim 0 FAST-TWO-SUM(a, b) (Theorem 1), 1 TWO-SUM(a, b) (Theorem 2),
    2 TwoProduct (p = RN(ab), e = fma(a, b, -p)); the binary64 forms the
    reductions use, with the error (and for 4 the product) computed on the
-   integer pipe from the significands: 3 TWO-SUM, 4 TwoProduct, 5 FAST-TWO-SUM,
-   and 6 TWO-SUM entirely on the integer pipe.  3-6 give the bits of 1, 2, 0, 1
-   (binary32 data use 1, 2, 0, 1).  Outputs to x, y. */
+   integer pipe from the significands: 3 TWO-SUM, 4 TwoProduct, 5 FAST-TWO-SUM.
+   3-5 give the bits of 1, 2, 0 (binary32 data use 1, 2, 0).  Outputs to x, y. */
 tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* x, void* y,
                   int64_t n, tf_stream_t stream);
 
 /* Memory-read probe (the paper's read1/read2): streams nbytes of x (and of y
-   when not NULL) with the reduction's 128-bit loads and no arithmetic, and
-   writes one word per block to sink (blocks words). */
+   when not NULL) with the reductions' 128-bit streaming loads and no
+   arithmetic, 8 loads in flight per thread for one array and 4 per array for
+   two, and writes one word per block to sink (blocks words). */
 tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
                         int32_t blocks, int32_t threads, tf_stream_t stream);
 
@@ -257,10 +257,8 @@ tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink
    iterations of 8 independent chains of one operation, from registers.
    kind: 0 FADD, 1 DADD, 2 FFMA, 3 DFMA, 4 IADD (32-bit), 5 fast step binary32,
    6 rigorous step binary32, 7 fast step binary64, 8 rigorous step binary64,
-   9 binary64 add issued as fma(a, 1, b), 10 DMUL, 11 binary32 -> binary64
-   conversion (with a dependent integer op per iteration), 12 binary64 add
-   issued as fma(a, one, b) with `one` = 1.0 read from constant memory,
-   13 the same with `one` computed at run time in a register.
+   9 DMUL, 10 binary64 add issued as fma(a, one, b) with `one` = 1.0 computed
+   at run time (how the binary64 sums issue their adds).
    sink receives one word per thread (blocks * threads words). */
 tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
                        tf_stream_t stream);

@@ -485,7 +485,7 @@ tf_status tf_count_large_errors(const void* pairs, int64_t npairs, tf_dtype pair
 
 tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* x, void* y,
                   int64_t n, tf_stream_t stream) {
-    if (prim < 0 || prim > 6 || n < 0 || (n > 0 && (!a || !b || !x || !y))) return TF_ERR_ARG;
+    if (prim < 0 || prim > 5 || n < 0 || (n > 0 && (!a || !b || !x || !y))) return TF_ERR_ARG;
     if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
     int sms = 0;
     tf_status s = check_device(&sms);
@@ -508,7 +508,7 @@ tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink
 
 tf_status tf_probe_alu(int kind, int64_t iters, void* sink, int32_t blocks, int32_t threads,
                        tf_stream_t stream) {
-    if (kind < 0 || kind > 13 || iters < 0 || !sink || blocks < 1 || threads < 32 ||
+    if (kind < 0 || kind > 10 || iters < 0 || !sink || blocks < 1 || threads < 32 ||
         threads > 1024 || threads % 32)
         return TF_ERR_ARG;
     int sms = 0;

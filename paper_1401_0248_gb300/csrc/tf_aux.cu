@@ -35,13 +35,6 @@ __global__ void prim_kernel(int prim, const T* __restrict__ a, const T* __restri
             } else {
                 two_sum(a[i], b[i], u, v);
             }
-        } else if (prim == 6) {      // binary64 TWO-SUM entirely on the integer pipe
-            if constexpr (sizeof(T) == 8) {
-                bool sw;
-                if (!two_sum_i64(a[i], b[i], u, v, sw)) two_sum(a[i], b[i], u, v);
-            } else {
-                two_sum(a[i], b[i], u, v);
-            }
         } else {                     // 4: binary64 TwoProduct on the integer pipe
             if constexpr (sizeof(T) == 8) {
                 if (!two_product_i64(a[i], b[i], u, v)) two_product(a[i], b[i], u, v);
@@ -95,35 +88,39 @@ cudaError_t launch_large_errors(const void* pairs, int64_t npairs, int dtype, do
 }
 
 // ------------------------------------------------------------ read probe
+// U 16-byte loads of each array in flight per thread and step: one array
+// takes 8 (128 bytes), two arrays 4 each, so that either form keeps as many
+// bytes in flight per thread as the reductions' best plans.
+template <int U, bool TWO>
 __global__ void __launch_bounds__(1024)
 read_probe(const float* __restrict__ x, const float* __restrict__ y, int64_t nvec,
            unsigned int* __restrict__ sink) {
     const int64_t P = (int64_t)gridDim.x * blockDim.x;
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int acc = 0;
-    for (; j + 3 * P < nvec; j += 4 * P) {
-        float r[4][4], q[4][4];
+    for (; j + (U - 1) * P < nvec; j += U * P) {
+        float r[U][4], q[U][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             ld_stream(x + 4 * (j + u * P), r[u]);
-            if (y) ld_stream(y + 4 * (j + u * P), q[u]);
+            if constexpr (TWO) ld_stream(y + 4 * (j + u * P), q[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 acc ^= __float_as_uint(r[u][l]);
-                if (y) acc ^= __float_as_uint(q[u][l]);
+                if constexpr (TWO) acc ^= __float_as_uint(q[u][l]);
             }
     }
     for (; j < nvec; j += P) {
         float r[4], q[4];
         ld_stream(x + 4 * j, r);
-        if (y) ld_stream(y + 4 * j, q);
+        if constexpr (TWO) ld_stream(y + 4 * j, q);
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
             acc ^= __float_as_uint(r[l]);
-            if (y) acc ^= __float_as_uint(q[l]);
+            if constexpr (TWO) acc ^= __float_as_uint(q[l]);
         }
     }
 #pragma unroll
@@ -140,14 +137,20 @@ read_probe(const float* __restrict__ x, const float* __restrict__ y, int64_t nve
 
 cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
                               int blocks, int threads, cudaStream_t st) {
-    read_probe<<<blocks, threads, 0, st>>>((const float*)x, (const float*)y, nbytes / 16,
-                                           (unsigned int*)sink);
+    if (y)
+        read_probe<4, true><<<blocks, threads, 0, st>>>((const float*)x, (const float*)y,
+                                                        nbytes / 16, (unsigned int*)sink);
+    else
+        read_probe<8, false><<<blocks, threads, 0, st>>>((const float*)x, nullptr, nbytes / 16,
+                                                         (unsigned int*)sink);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- ALU probe
-__constant__ double kProbeOne = 1.0;     // opaque to the compiler: a runtime 1.0
-
+// kind: 0 FADD, 1 DADD, 2 FFMA, 3 DFMA, 4 IADD (32-bit), 5 / 6 the binary32
+// fast / rigorous step, 7 / 8 the binary64 fast / rigorous step, 9 DMUL,
+// 10 a binary64 add issued as fma(a, one, b) with `one` = 1.0 computed at run
+// time (the form the binary64 sums use, see dadd in tf_device.cuh).
 template <int KIND>
 __global__ void __launch_bounds__(1024)
 alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
@@ -169,9 +172,12 @@ alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) out ^= __float_as_uint(c[k]) ^ __float_as_uint(e[k]);
-    } else if constexpr (KIND == 1 || KIND == 3 || KIND == 7 || KIND == 8) {
+    } else if constexpr (KIND == 1 || KIND == 3 || KIND == 7 || KIND == 8 || KIND == 9 ||
+                         KIND == 10) {
         double c[8], e[8];
         const double d = (double)seed * 1e-15, m = 1.0 - (double)seed * 1e-17;
+        // a 1.0 the compiler cannot see (it would fold a known 1.0 into a DADD)
+        const double one = (double)(seed > 0.0f) + (double)(iters < 0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) { c[k] = (double)seed + (double)(tid + k); e[k] = 0.0; }
         for (int64_t it = 0; it < iters; ++it) {
@@ -180,52 +186,15 @@ alu_probe(int64_t iters, unsigned int* __restrict__ sink, float seed) {
                 if constexpr (KIND == 1) c[k] = __dadd_rn(c[k], d);
                 else if constexpr (KIND == 3) c[k] = __fma_rn(c[k], m, d);
                 else if constexpr (KIND == 7) feed<FAST, false>(c[k], e[k], d, 0.0);
-                else feed<RIGOROUS, false>(c[k], e[k], d, 0.0);
+                else if constexpr (KIND == 8) feed<RIGOROUS, false>(c[k], e[k], d, 0.0);
+                else if constexpr (KIND == 9) c[k] = __dmul_rn(c[k], m);
+                else c[k] = __fma_rn(c[k], one, d);
             }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             unsigned long long b = __double_as_longlong(c[k]) ^ __double_as_longlong(e[k]);
             out ^= (unsigned int)b ^ (unsigned int)(b >> 32);
-        }
-    } else if constexpr (KIND == 12 || KIND == 13) {
-        // binary64 add issued as fma(a, one, b) with `one` = 1.0 read from constant
-        // memory (12) or computed from a runtime value in a register (13)
-        double c[8];
-        const double one = KIND == 12 ? kProbeOne : (double)(seed > 0.0f) + (double)(iters < 0);
-        const double d = (double)seed * 1e-15;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) c[k] = (double)seed + (double)(tid + k);
-        for (int64_t it = 0; it < iters; ++it) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) c[k] = __fma_rn(c[k], one, d);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            unsigned long long b = __double_as_longlong(c[k]);
-            out ^= (unsigned int)b ^ (unsigned int)(b >> 32);
-        }
-    } else if constexpr (KIND == 9 || KIND == 10 || KIND == 11) {
-        // 9: binary64 add written as fma(a, 1, b); 10: DMUL; 11: binary32 -> binary64 convert
-        double c[8];
-        float f[8];
-        double one;
-        asm volatile("mov.b64 %0, 0x3FF0000000000000;" : "=d"(one));
-        const double d = (double)seed * 1e-15, m = 1.0 - (double)seed * 1e-17;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) { c[k] = (double)seed + (double)(tid + k); f[k] = seed + k; }
-        for (int64_t it = 0; it < iters; ++it) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if constexpr (KIND == 9) c[k] = __fma_rn(c[k], one, d);
-                else if constexpr (KIND == 10) c[k] = __dmul_rn(c[k], m);
-                else { c[k] = (double)f[k]; f[k] = __int_as_float(__float_as_int(f[k]) ^ (int)__double2hiint(c[k])); }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            unsigned long long b = __double_as_longlong(c[k]);
-            out ^= (unsigned int)b ^ (unsigned int)(b >> 32) ^ __float_as_uint(f[k]);
         }
     } else {  // KIND 4: 32-bit integer adds
         unsigned int c[8];
@@ -258,9 +227,6 @@ cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, in
     case 8: alu_probe<8><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     case 9: alu_probe<9><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     case 10: alu_probe<10><<<blocks, threads, 0, st>>>(iters, s, seed); break;
-    case 11: alu_probe<11><<<blocks, threads, 0, st>>>(iters, s, seed); break;
-    case 12: alu_probe<12><<<blocks, threads, 0, st>>>(iters, s, seed); break;
-    case 13: alu_probe<13><<<blocks, threads, 0, st>>>(iters, s, seed); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

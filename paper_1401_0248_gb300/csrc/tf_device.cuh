@@ -47,83 +47,6 @@ __device__ __forceinline__ void two_sum(T a, T b, T& x, T& y) {
     y = add_rn(as, bs);
 }
 
-// TWO-SUM of two binary64 numbers on the integer pipe (GB300 issues 32-bit
-// integer operations at 64 times its binary64 rate).  x = RN(a + b) and
-// y = a + b - x are computed exactly from the integer significands:
-//   order |a| >= |b|; d = ea - eb; if d >= 55, |b| < ulp(a)/4 so x = a, y = b;
-//   else S = ma*2^d +- mb exactly (at most 108 bits), x = S rounded to 53
-//   bits to nearest even, y = the signed remainder (exact by Theorem 2).
-// Returns false, leaving x and y untouched, when an operand is zero,
-// subnormal, below 2^-969 or above 2^1021, or not finite; callers then use
-// the binary64 TWO-SUM.  Both routes give the same bits.  *swapped reports
-// |a| < |b| (the precondition of Theorem 1 fails).
-__device__ __forceinline__ bool two_sum_i64(double a, double b, double& x, double& y,
-                                            bool& swapped) {
-    unsigned long long A = (unsigned long long)__double_as_longlong(a);
-    unsigned long long B = (unsigned long long)__double_as_longlong(b);
-    const unsigned long long MAG = 0x7fffffffffffffffull, M52 = 0x000fffffffffffffull;
-    unsigned long long absA = A & MAG, absB = B & MAG;
-    swapped = absA < absB;
-    if (swapped) {
-        unsigned long long t = A; A = B; B = t;
-        t = absA; absA = absB; absB = t;
-    }
-    const int ea = (int)(absA >> 52), eb = (int)(absB >> 52);
-    if (eb < 54 || ea > 2044) return false;
-    const unsigned long long sa = A >> 63;
-    const int d = ea - eb;
-    if (d >= 55) {                    // |b| < ulp(a)/4: RN(a + b) = a, error b
-        x = __longlong_as_double((long long)A);
-        y = __longlong_as_double((long long)B);
-        return true;
-    }
-    const unsigned long long ma = (absA & M52) | (1ull << 52);
-    const unsigned long long mb = (absB & M52) | (1ull << 52);
-    unsigned long long lo = ma << d;
-    unsigned long long hi = d ? (ma >> (64 - d)) : 0ull;
-    if ((A ^ B) >> 63) {              // opposite signs: S = ma*2^d - mb >= 0
-        hi -= (lo < mb) ? 1ull : 0ull;
-        lo -= mb;
-    } else {
-        lo += mb;
-        hi += (lo < mb) ? 1ull : 0ull;
-    }
-    if ((hi | lo) == 0ull) {          // exact cancellation: +0, +0
-        x = 0.0;
-        y = 0.0;
-        return true;
-    }
-    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-    int sh = p - 52;                  // bits below the 53-bit window
-    if (sh <= 0) {                    // S fits in 53 bits: exact sum, error +0
-        const unsigned long long q = lo << (-sh);
-        x = __longlong_as_double((long long)((sa << 63) |
-                                             ((unsigned long long)(eb + p - 52) << 52) | (q & M52)));
-        y = 0.0;
-        return true;
-    }
-    // 1 <= sh <= 56: q = S >> sh (< 2^53), rem = S mod 2^sh (from lo alone)
-    unsigned long long q = (lo >> sh) | (hi << (64 - sh));
-    const unsigned long long rem = lo & ((1ull << sh) - 1ull);
-    const unsigned long long half = 1ull << (sh - 1);
-    const bool up = rem > half || (rem == half && (q & 1ull));
-    const unsigned long long rmag = up ? ((1ull << sh) - rem) : rem;
-    q += up ? 1ull : 0ull;
-    int ex = eb + sh;                 // biased exponent of q*2^(sh + eb - 1075)
-    if (q == (1ull << 53)) { q >>= 1; ex += 1; }
-    x = __longlong_as_double((long long)((sa << 63) | ((unsigned long long)ex << 52) | (q & M52)));
-    if (rmag == 0ull) {
-        y = 0.0;
-    } else {
-        const int pr = 63 - __clzll((long long)rmag);
-        const unsigned long long mr = pr > 52 ? (rmag >> (pr - 52)) : (rmag << (52 - pr));
-        const unsigned long long sy = sa ^ (up ? 1ull : 0ull);
-        y = __longlong_as_double((long long)((sy << 63) |
-                                             ((unsigned long long)(eb + pr - 52) << 52) | (mr & M52)));
-    }
-    return true;
-}
-
 // Exact binary32 -> binary64 widening on the integer pipe (GB300's binary64
 // conversion shares the slow binary64 rate): sign, exponent + 896, significand
 // shifted by 29.  False for subnormal, infinite or NaN inputs (callers then

@@ -374,7 +374,7 @@ def plan_load(path):
 
 # --------------------------------------------------------- building blocks
 PRIMS = {"fast_two_sum": 0, "two_sum": 1, "two_product": 2, "two_sum_int": 3,
-         "two_product_int": 4, "fast_two_sum_int": 5, "two_sum_allint": 6}
+         "two_product_int": 4, "fast_two_sum_int": 5}
 
 
 def prim(name, a, b):
@@ -399,10 +399,10 @@ def probe_read(x, y=None, blocks=None, threads=512, sink=None):
 
 
 ALU_KINDS = {"fadd": 0, "dadd": 1, "ffma": 2, "dfma": 3, "iadd": 4, "fast_f32": 5,
-             "rigorous_f32": 6, "fast_f64": 7, "rigorous_f64": 8, "dadd_as_fma": 9,
-             "dmul": 10, "cvt_f32_f64": 11, "dadd_as_fma_const": 12, "dadd_as_fma_reg": 13}
-ALU_OPS_PER_ITER = {0: 8, 1: 8, 2: 8, 3: 8, 4: 8, 5: 32, 6: 56, 7: 32, 8: 56, 9: 8, 10: 8, 11: 8,
-                    12: 8, 13: 8}
+             "rigorous_f32": 6, "fast_f64": 7, "rigorous_f64": 8, "dmul": 9, "dadd_as_fma": 10}
+# operations per thread per iteration (8 chains; the step mixes count the
+# paper's 4 and 7 operations per item)
+ALU_OPS_PER_ITER = {0: 8, 1: 8, 2: 8, 3: 8, 4: 8, 5: 32, 6: 56, 7: 32, 8: 56, 9: 8, 10: 8}
 
 
 def probe_alu(kind, iters, blocks, threads, sink=None, device=None):

@@ -121,10 +121,6 @@ def test_int_two_sum_f64_bit_exact():
     assert same_bits(_np(gx), _np(hx)) and same_bits(_np(gy), _np(hy))
     gx, gy = tf.prim("two_sum_int", tb, ta)          # operand order
     assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
-    gx, gy = tf.prim("two_sum_allint", ta, tb)        # all-integer form
-    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
-    gx, gy = tf.prim("two_sum_allint", tb, ta)
-    assert same_bits(_np(gx), wx) and same_bits(_np(gy), wy)
 
 
 def test_int_fast_two_sum_f64_bit_exact():
