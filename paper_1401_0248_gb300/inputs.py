@@ -15,6 +15,10 @@ The workloads follow the paper's and the benchmark's shapes: uniform data on
 [-1, 1) (the paper's accuracy table), N(0,1) and signed log-normal(0, 2)
 vectors, ragged CSR batches with log-uniform lengths, and ill-conditioned
 vectors whose exact sum is known by construction (``ill_conditioned``).
+``exact_dot_f32`` gives the known exact dot of a binary32 pair (each product
+is an integer significand product times a power of two; the integers are
+added exactly in 31-bit limbs), for reporting accuracy at sizes where no
+construction fixes it.
 """
 from __future__ import annotations
 
@@ -202,3 +206,50 @@ class IllConditioned:
 
 def ill_conditioned(n, dtype="f64", cond=1e8, seed=0, device="cpu", dot=False):
     return IllConditioned(n, dtype, cond, seed, device, dot)
+
+
+# ------------------------------------------------- exact binary32 dot value
+_LIMB = 31
+_EMIN32 = -149 - 149          # exponent of the least product's unit
+
+
+def exact_dot_f32(x: torch.Tensor, y: torch.Tensor) -> Fraction:
+    """The exact real sum of x_i * y_i for finite binary32 vectors, as a Fraction.
+
+    Each x_i = mx * 2^ex with an integer significand mx < 2^24 (subnormals
+    included), so x_i * y_i = (mx * my) * 2^(ex + ey), an integer below 2^48
+    times a power of two.  Split into 24-bit halves and placed at bit offset
+    ex + ey + 298 >= 0, every half lands in two 31-bit limbs; the limbs are
+    added as int64 (each partial sum stays below 2^62 for up to 2^30 items)
+    and combined as an exact integer.  No floating-point arithmetic touches
+    the values; runs on the tensors' device, a chunk at a time."""
+    assert x.dtype == torch.float32 and y.dtype == torch.float32 and x.shape == y.shape
+    n = x.numel()
+    assert n < (1 << 30) + 1, "limb sums are exact for at most 2^30 items"
+    nlimb = (2 * 149 + 2 * 128 + 48) // _LIMB + 3
+    acc = torch.zeros(nlimb, dtype=torch.int64, device=x.device)
+    mask = (1 << _LIMB) - 1
+    xf, yf = x.reshape(-1), y.reshape(-1)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        parts = []
+        for t in (xf[a:b], yf[a:b]):
+            u = t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+            e = (u >> 23) & 0xFF
+            assert not bool((e == 0xFF).any()), "finite data only"
+            m = (u & 0x7FFFFF) | torch.where(e > 0, 1 << 23, 0)
+            parts.append((m, torch.clamp(e, min=1) - 150, u >> 31))
+        (mx, ex, sx), (my, ey, sy) = parts
+        M = mx * my                                        # < 2^48, exact
+        off = ex + ey - _EMIN32                            # >= 0
+        sign = 1 - 2 * (sx ^ sy)
+        for half, shift in ((M & 0xFFFFFF, 0), (M >> 24, 24)):
+            pos = off + shift
+            limb = pos // _LIMB
+            v = half << (pos % _LIMB)                       # < 2^54
+            acc.index_add_(0, limb, sign * (v & mask))
+            acc.index_add_(0, limb + 1, sign * (v >> _LIMB))
+    total = 0
+    for k, c in enumerate(acc.tolist()):
+        total += c << (_LIMB * k)
+    return Fraction(total) * (Fraction(2) ** _EMIN32)

@@ -47,3 +47,24 @@ def test_csr_lengths_and_offsets():
     # log-uniform lengths: the mean of [16, 2^18] is (2^18 - 16) / ln(2^14)
     mean = (2 ** 18 - 16) / np.log(2 ** 14)
     assert 0.9 * mean < float(np.mean(L)) < 1.1 * mean
+
+
+def test_exact_dot_f32_against_fractions_and_oracle():
+    """The known exact dot of a binary32 pair (limb sums of the integer
+    significand products) equals brute-force rational arithmetic on small
+    vectors with subnormals, zeros and huge values, and the oracle's exact
+    superaccumulator on larger N(0,1) and signed log-normal pairs."""
+    from fractions import Fraction
+    import oracle as O
+    x = torch.tensor([1e-45, -3e-39, 3e38, 1.0, 0.0, -0.0, 2.5e-20, 7.0], dtype=torch.float32)
+    y = torch.tensor([1e-45, 2e-39, -3e38, -0.0, 5.0, 3.0, 3.3e-21, -1.0 / 3], dtype=torch.float32)
+    want = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x.tolist(), y.tolist()))
+    assert I.exact_dot_f32(x, y) == want
+    for gen in (I.normal, I.signed_lognormal):
+        a = gen(200003, "f32", seed=3)
+        b = gen(200003, "f32", seed=3, stream=6)
+        S = I.exact_dot_f32(a, b)
+        ex = O.exact(a.numpy(), b.numpy(), v=float(S))
+        assert ex.s == float(S) and ex.s32 == np.float32(float(S))
+        # the residual of RN64(S) is below half an ulp: S is exact, not rounded
+        assert abs(ex.rv) <= abs(float(S)) * 2.0 ** -53
