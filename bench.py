@@ -15,9 +15,17 @@ value    whole-step algorithmic bytes / device time (CUDA events, inputs
 e2e      the same step through the C ABI's host-buffer calls: pinned host
          inputs copied to the device inside the timed region, the result pair
          copied back.
-roofline the kernel with the largest share of the step time, against the
-         measured HBM copy bandwidth or, for binary64 kernels bound by the
-         binary64 pipe, against the binary64 instruction peak.
+roofline the kernel with the largest share of the step time: its algorithmic
+         bytes per launch / its CUDA-event time against the measured HBM copy
+         bandwidth; for binary64 kernels, which the binary64 pipe limits,
+         also ("alu") its issued binary64 adds against that pipe's measured
+         rate.
+c3, c5   the two large dot configurations beside the step: binary32 dots of
+         N = 2^30 (N(0,1) and signed log-normal(0, 2) data) and binary64 dots
+         of N = 2^29 (condition numbers 1e8 .. 1e30), each variant timed, with
+         relative errors against the exact dot and the error term's tracking
+         of the value's own error; C5 also checks 20 repeated runs for
+         identical bits.
 cpu_baseline  the CPU oracle's sequential loops (the paper's twofold loops)
          timed on a bounded sample of the same workload on one host core.
 
@@ -326,14 +334,15 @@ def run_gpu(args, rank, world, local):
     value = total_bytes / (step_ms * 1e-3) / 1e9
 
     # per-kernel report and accuracy: fractions of the measured copy rate, of
-    # the measured two-array read rate (probe) and of the nominal 7.9 TB/s
+    # the measured read rate of as many arrays (probe: one array for sums,
+    # two for dots) and of the nominal 7.9 TB/s
     hbm, peak_kind = load_peaks()
-    read_bw = (probes or {}).get("read2_gbs")
     kernels, accuracy = {}, {}
     for k in ks_all:
         dt, cond, op, v, _ = k
         ms = kern_ms.get(k, base_ms.get(k))
         gbs = nbytes(dt, op, n) / (ms * 1e-3) / 1e9
+        read_bw = (probes or {}).get("read2_gbs" if op == "dot" else "read1_gbs")
         name = "%s_%s_%s_c%g" % (dt, op, v, cond)
         kernels[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4),
                          "frac_read": round(gbs / read_bw, 4) if read_bw else None,
@@ -387,28 +396,30 @@ def run_gpu(args, rank, world, local):
     except Exception:
         pass
     bytes_dom = nbytes(dt, op, n)
+    ach = bytes_dom / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": traffic, "kernel": dom_name,
+                "bytes_per_launch": bytes_dom, "ms_per_launch": round(dom_ms, 4),
+                "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % peak_kind
+                if peak_kind == "measured" else "fallback HBM figure (no MEASURED_PEAKS.json)"}
     if dt == "f64":
-        # bound by the binary64 pipe: its issued adds against the measured rate
-        # of the instruction they use (DFMA by 1.0 for sums, DADD for dots)
+        # what limits the binary64 kernels: the binary64 pipe (with the exact
+        # error terms on the integer pipe); its issued adds against the
+        # measured rate of the instruction they use (DFMA by 1.0 for sums,
+        # DADD for dots)
         fma_adds = op == "sum"
         peak_ops = (probes or {}).get("dadd_as_fma_gops" if fma_adds else "dadd_gops") \
             or (FALLBACK_DFMA_GOPS if fma_adds else FALLBACK_DADD_GOPS)
         ops = FP64_PIPE_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": round(ops, 1), "peak": round(peak_ops, 1),
-                    "unit": "G binary64-pipe ops/s", "frac": round(ops / peak_ops, 4),
-                    "traffic": traffic, "kernel": dom_name,
-                    "peak_source": ("measured rate of binary64 adds issued as DFMA by a runtime "
-                                    "1.0 (probe kind 10) on this GPU" if fma_adds else
-                                    "measured binary64 add rate (probe kind 1) on this GPU")
-                                   if probes else "fallback (no probes)",
-                    "paper_ops_per_s_g": round(PAPER_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9, 1),
-                    "hbm_gbs": round(bytes_dom / (dom_ms * 1e-3) / 1e9, 1),
-                    "hbm_frac": round(bytes_dom / (dom_ms * 1e-3) / 1e9 / hbm, 4)}
-    else:
-        ach = bytes_dom / (dom_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(ach / hbm, 4), "traffic": traffic, "kernel": dom_name,
-                    "peak_source": peak_kind}
+        roofline["alu"] = {
+            "achieved": round(ops, 1), "peak": round(peak_ops, 1),
+            "unit": "G binary64-pipe ops/s", "frac": round(ops / peak_ops, 4),
+            "ops_per_element": FP64_PIPE_OPS[(op, v)],
+            "peak_source": ("measured rate of binary64 adds issued as DFMA by a runtime 1.0 "
+                            "(probe kind 10) on this GPU" if fma_adds else
+                            "measured binary64 add rate (probe kind 1) on this GPU")
+            if probes else "fallback (no probes)",
+            "paper_ops_per_s_g": round(PAPER_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9, 1)}
 
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
@@ -439,17 +450,23 @@ def run_probes(data, dev, stream, cond0):
     sms = tf.sm_count()
     out = {}
     x, y, _, _ = data[("f64", cond0)]["dot"]
+    # the best of a few launch shapes (the probe's own roofline, as the
+    # paper's read1/read2 are the best of its read loops)
     for name, args_ in (("read1_gbs", (x, None)), ("read2_gbs", (x, y))):
         b = x.numel() * 8 * (2 if args_[1] is not None else 1)
         best = 1e30
-        for _ in range(5):
-            a = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            tf.probe_read(args_[0], args_[1], blocks=4 * sms, threads=512)
-            e.record(stream)
-            torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(e))
+        for bps in (2, 4, 8):
+            for threads in (256, 512, 1024):
+                if bps * threads > 2048:
+                    continue
+                for _ in range(3):
+                    a = torch.cuda.Event(enable_timing=True)
+                    e = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    tf.probe_read(args_[0], args_[1], blocks=bps * sms, threads=threads)
+                    e.record(stream)
+                    torch.cuda.synchronize()
+                    best = min(best, a.elapsed_time(e))
         out[name] = round(b / (best * 1e-3) / 1e9, 1)
     blocks, threads = 4 * sms, 256
     for kind, iters in (("fadd", 20000), ("dadd", 2000), ("dfma", 2000), ("iadd", 20000),
@@ -465,6 +482,112 @@ def run_probes(data, dev, stream, cond0):
         ops = tf.ALU_OPS_PER_ITER[tf.ALU_KINDS[kind]] * iters * blocks * threads
         out[kind + "_gops"] = round(ops / (a.elapsed_time(e) * 1e-3) / 1e9, 1)
     return out
+
+
+def _time_calls(call, stream, warmup, reps):
+    for _ in range(warmup):
+        call()
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        call()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _accuracy_entry(S, sabs, o, twofold):
+    acc = {"rel_err_v_plus_e": rel_err(S, o[0], o[1]), "rel_err_v": rel_err(S, o[0])}
+    if twofold:
+        rv = S - Fraction(float(o[0]))
+        acc["e_over_residual"] = float(Fraction(float(o[1])) / rv) if rv != 0 else None
+    return acc
+
+
+def run_c3(args, dev, stream, hbm):
+    """Binary32 twofold dots of N = 2^30 per vector (4 GiB each): N(0,1) and
+    signed log-normal(0, 2) data; binary32 arithmetic with a binary64 merge
+    across blocks, beside the binary64 accumulator ('wide') and the plain
+    binary32 dot, each against the exact dot (integer limb sums)."""
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    from paper_1401_0248_gb300 import twofold as tf
+    n = args.c3_n
+    res = {"config": "binary32 dot, N=%d per vector, N(0,1) and signed log-normal(0,2), seed 0" % n,
+           "kernels": {}}
+    ws = torch.zeros(tf.workspace_size("dot", False, torch.float32, "fast", n), dtype=torch.uint8,
+                     device=dev)
+    for dist in ("normal", "lognormal"):
+        if dist == "normal":
+            x = I.normal(n, "f32", seed=0, stream=0, device=dev)
+            y = I.normal(n, "f32", seed=0, stream=3, device=dev)
+        else:
+            x = I.signed_lognormal(n, "f32", seed=0, stream=0, device=dev)
+            y = I.signed_lognormal(n, "f32", seed=0, stream=5, device=dev)
+        S = I.exact_dot_f32(x, y)
+        sabs = 0.0
+        for a in range(0, n, 1 << 26):
+            sabs += float(torch.sum(torch.abs(x[a:a + (1 << 26)].double() * y[a:a + (1 << 26)].double())))
+        ent = {"cond": float("%.3g" % (sabs / abs(float(S)))), "variants": {}}
+        out = torch.empty(2, dtype=torch.float32, device=dev)
+        for v in ("fast", "rigorous", "wide", "plain"):
+            ms = _time_calls(lambda: tf.dot(x, y, v, out=out, ws=ws), stream, args.warmup,
+                             max(5, min(args.steps, 10)))
+            gbs = nbytes("f32", "dot", n) / (ms * 1e-3) / 1e9
+            o = out.cpu().tolist()
+            e = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4)}
+            e.update(_accuracy_entry(S, sabs, o, v in TWOFOLD))
+            ent["variants"][v] = e
+        for v in TWOFOLD:
+            ent["variants"][v]["vs_plain_time"] = round(ent["variants"][v]["ms"] /
+                                                       ent["variants"]["plain"]["ms"], 4)
+        res["kernels"][dist] = ent
+        del x, y
+        torch.cuda.empty_cache()
+    return res
+
+
+def run_c5(args, dev, stream, hbm):
+    """Binary64 twofold dots of N = 2^29 per vector (4 GiB each) on
+    ill-conditioned data (condition numbers 1e8, 1e16, 1e24, 1e30; exact dot
+    known by construction), fast against rigorous beside the plain dot, with
+    the error term's tracking of the value's error and 20 repeated runs of
+    each twofold variant checked for identical bits."""
+    import torch
+    from paper_1401_0248_gb300 import inputs as I
+    from paper_1401_0248_gb300 import twofold as tf
+    n = args.c5_n
+    res = {"config": "binary64 dot, N=%d per vector, ill-conditioned, seed 0" % n, "kernels": {}}
+    ws = torch.zeros(tf.workspace_size("dot", False, torch.float64, "fast", n), dtype=torch.uint8,
+                     device=dev)
+    for cond in (1e8, 1e16, 1e24, 1e30):
+        ic = I.ill_conditioned(n, "f64", cond, seed=0, device=dev, dot=True)
+        ent = {"cond": float("%.3g" % ic.cond), "variants": {}}
+        out = torch.empty(2, dtype=torch.float64, device=dev)
+        for v in ("fast", "rigorous", "plain"):
+            ms = _time_calls(lambda: tf.dot(ic.x, ic.y, v, out=out, ws=ws), stream, args.warmup,
+                             max(5, min(args.steps, 10)))
+            gbs = nbytes("f64", "dot", n) / (ms * 1e-3) / 1e9
+            o = out.cpu().tolist()
+            e = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4)}
+            e.update(_accuracy_entry(ic.S, ic.sum_abs, o, v in TWOFOLD))
+            if v in TWOFOLD:
+                ref = out.clone()
+                same = True
+                for _ in range(20):
+                    tf.dot(ic.x, ic.y, v, out=out, ws=ws)
+                    same = same and bool(torch.equal(out.view(torch.int64), ref.view(torch.int64)))
+                e["bits_identical_20_runs"] = same
+            ent["variants"][v] = e
+        for v in TWOFOLD:
+            ent["variants"][v]["vs_plain_time"] = round(ent["variants"][v]["ms"] /
+                                                       ent["variants"]["plain"]["ms"], 4)
+        res["kernels"]["c%g" % cond] = ent
+        del ic
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_small(dev, stream, reps=20):
@@ -854,6 +977,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probes", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the N=2^30 / 2^29 dot configurations")
+    ap.add_argument("--c3-n", type=int, default=1 << 30)
+    ap.add_argument("--c5-n", type=int, default=1 << 29)
     ap.add_argument("--no-clocks", action="store_true", help="profiling: no nvidia-smi sampler")
     ap.add_argument("--only", default="", help="profiling: comma list of kernels, e.g. f64_dot_rigorous")
     ap.add_argument("--conds", default="1e4,1e8,1e16", help="profiling: condition numbers")
@@ -880,6 +1006,11 @@ def main(argv=None):
                                      torch.cuda.current_stream(torch.device("cuda", local)))
         res["small"] = run_small(torch.device("cuda", local),
                                  torch.cuda.current_stream(torch.device("cuda", local)))
+    if not args.no_large:
+        d = torch.device("cuda", local)
+        hbm, _ = load_peaks()
+        res["c3"] = run_c3(args, d, torch.cuda.current_stream(d), hbm)
+        res["c5"] = run_c5(args, d, torch.cuda.current_stream(d), hbm)
     if not args.no_e2e:
         e2e = run_e2e(args, data, ws, step_ks, torch.device("cuda", local))
         e2e["value"] = round(sum_over_ranks(e2e["value"], world), 2) if world > 1 else e2e["value"]
