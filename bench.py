@@ -12,9 +12,10 @@ run alongside on the same data and are reported per kernel, not in the step.
 
 value    whole-step algorithmic bytes / device time (CUDA events, inputs
          resident in HBM, every input larger than L2).
-e2e      the same step through the C ABI's host-buffer calls: pinned host
-         inputs copied to the device inside the timed region, the result pair
-         copied back.
+e2e      the same step through the C ABI's asynchronous host-buffer calls:
+         pinned host inputs copied to the device inside the timed region (on
+         a copy stream, each reduction ordered behind its copy), the result
+         pairs copied back, one host wait per step.
 roofline the kernel with the largest share of the step time: its algorithmic
          bytes per launch / its CUDA-event time against the measured HBM copy
          bandwidth; for binary64 kernels, which the binary64 pipe limits,
@@ -29,10 +30,13 @@ c3, c5   the two large dot configurations beside the step: binary32 dots of
 cpu_baseline  the CPU oracle's sequential loops (the paper's twofold loops)
          timed on a bounded sample of the same workload on one host core.
 
-Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--split]
 Under torchrun (N > 1) each rank reduces its own copy of the workload (the
 path shards into independent problems, no collective on the data path); the
 step time is the maximum over ranks and value counts all ranks' bytes.
+--split instead cuts every vector into N contiguous shards, one per rank,
+gathers the N shard pairs and merges them in rank order on each rank
+(strong scaling; one 16-byte all-gather per reduction).
 """
 from __future__ import annotations
 
@@ -146,6 +150,19 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def gather_pairs(pair, world):
+    """Every rank's shard pair in rank order: a (world, 2) tensor on the
+    pair's device, from one all-gather of 16 bytes per rank (the only data
+    exchange of a vector split over several GPUs)."""
+    import torch
+    if world <= 1:
+        return pair.reshape(1, 2)
+    import torch.distributed as dist
+    parts = [torch.empty_like(pair) for _ in range(world)]
+    dist.all_gather(parts, pair.contiguous())
+    return torch.stack(parts)
 
 
 # ------------------------------------------------------------------ clocks
@@ -442,6 +459,82 @@ def run_gpu(args, rank, world, local):
     return result, data, ws, outs, ks_all, step_ks
 
 
+def run_split(args, rank, world, local):
+    """One vector per reduction cut into `world` contiguous shards: each rank
+    reduces its shard (binary64 pair output), the pairs are all-gathered in
+    rank order and merged on the device (tf_merge_pairs).  Total work is
+    fixed as the rank count grows ("scaling": "strong"); the step time is the
+    slowest rank's, gather and merge included."""
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if os.path.exists(PLANS_PATH):
+        tf.plan_load(PLANS_PATH)
+    n = args.n
+    data = build_workload(n, dev, seed=0, conds=args.conds)     # the same vectors on every rank
+    step_ks = kernel_list(False, args.conds, args.only)
+    wsz = max(tf.workspace_size(op, False, torch.float32 if dt == "f32" else torch.float64, v, n)
+              for dt, _, op, v, _ in step_ks)
+    ws = torch.zeros(wsz, dtype=torch.uint8, device=dev)
+    pair = {k: torch.empty(2, dtype=torch.float64, device=dev) for k in step_ks}
+    outs = {k: torch.empty(2, dtype=torch.float32 if k[0] == "f32" else torch.float64, device=dev)
+            for k in step_ks}
+    stream = torch.cuda.current_stream(dev)
+
+    def launch(k):
+        dt, cond, op, v, _ = k
+        x, y, _, _ = data[(dt, cond)][op]
+        a, b = tf.shard_bounds(n, world, x.dtype)[rank]
+        if op == "sum":
+            tf.sum(x[a:b], v, out_f64=True, out=pair[k], ws=ws)
+        else:
+            tf.dot(x[a:b], y[a:b], v, out_f64=True, out=pair[k], ws=ws)
+        tf.merge_pairs(gather_pairs(pair[k], world), x.dtype, v, out=outs[k])
+
+    for _ in range(args.warmup):
+        for k in step_ks:
+            launch(k)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local, enabled=not args.no_clocks) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            for k in step_ks:
+                launch(k)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    step_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
+    total_bytes = sum(nbytes(k[0], k[2], n) for k in step_ks)
+    accuracy = {}
+    for k in step_ks:
+        dt, cond, op, v, _ = k
+        S = data[(dt, cond)][op][2]
+        o = outs[k].cpu().tolist()
+        accuracy["%s_%s_%s_c%g" % (dt, op, v, cond)] = {
+            "rel_err_v_plus_e": rel_err(S, o[0], o[1]), "rel_err_v": rel_err(S, o[0])}
+    return {
+        "metric": METRIC, "value": round(total_bytes / (step_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded SplitMix64; ill-conditioned, exact sum known by construction)",
+        "config": {"workload": "single vectors N=2^28 split over the ranks, f32+f64, twofold "
+                               "sum+dot, fast+rigorous, cond 1e4/1e8/1e16 (24 reductions per step)",
+                   "n": n, "conds": list(args.conds), "l2": "inputs larger than L2",
+                   "parallelism": "split: one vector in %d contiguous shards, shard pairs "
+                                  "all-gathered and merged in rank order" % world},
+        "gpu_launches": 2 * len(step_ks) * args.steps,
+        "clocks": clk.summary(),
+        "accuracy": accuracy,
+    }
+
+
 def run_probes(data, dev, stream, cond0):
     """Read bandwidth (the paper's read1/read2) and arithmetic rates (its
     p-functions) of this GPU, measured with the library's probe kernels."""
@@ -450,24 +543,26 @@ def run_probes(data, dev, stream, cond0):
     sms = tf.sm_count()
     out = {}
     x, y, _, _ = data[("f64", cond0)]["dot"]
-    # the best of a few launch shapes (the probe's own roofline, as the
-    # paper's read1/read2 are the best of its read loops)
-    for name, args_ in (("read1_gbs", (x, None)), ("read2_gbs", (x, y))):
-        b = x.numel() * 8 * (2 if args_[1] is not None else 1)
+    xs = data[("f32", cond0)]["sum"][0]
+    # the best of a few launch shapes and of the step's 1 and 2 GiB arrays
+    # (the probe's own roofline, as the paper's read1/read2 are the best of
+    # its read loops)
+    for name, args_ in (("read1_gbs", (x, None)), ("read1_gbs", (xs, None)),
+                        ("read2_gbs", (x, y))):
+        b = args_[0].numel() * args_[0].element_size() * (2 if args_[1] is not None else 1)
         best = 1e30
-        for bps in (2, 4, 8):
-            for threads in (256, 512, 1024):
-                if bps * threads > 2048:
-                    continue
-                for _ in range(3):
+        for unroll in (1, 2, 4, 8):
+            for bps, threads in ((2, 512), (4, 512), (2, 1024), (8, 256), (4, 256)):
+                for _ in range(5):
                     a = torch.cuda.Event(enable_timing=True)
                     e = torch.cuda.Event(enable_timing=True)
                     a.record(stream)
-                    tf.probe_read(args_[0], args_[1], blocks=bps * sms, threads=threads)
+                    tf.probe_read(args_[0], args_[1], blocks=bps * sms, threads=threads,
+                                  unroll=unroll)
                     e.record(stream)
                     torch.cuda.synchronize()
                     best = min(best, a.elapsed_time(e))
-        out[name] = round(b / (best * 1e-3) / 1e9, 1)
+        out[name] = max(out.get(name, 0.0), round(b / (best * 1e-3) / 1e9, 1))
     blocks, threads = 4 * sms, 256
     for kind, iters in (("fadd", 20000), ("dadd", 2000), ("dfma", 2000), ("iadd", 20000),
                         ("fast_f32", 5000), ("rigorous_f32", 3000), ("fast_f64", 500),
@@ -751,7 +846,11 @@ def gpu_numa_cpus(dev):
 
 
 def run_e2e(args, data, ws, step_ks, dev):
-    """The step through the host-buffer C-ABI calls (pinned inputs)."""
+    """The step through the asynchronous host-buffer C-ABI calls: each
+    reduction's pinned inputs are copied to its own device buffers on a copy
+    stream, the reduction runs on the compute stream behind its copy (an
+    event), its pair comes back to pinned host memory, and the host waits
+    once per step."""
     import torch
     from paper_1401_0248_gb300 import twofold as tf
     numa = gpu_numa_cpus(dev)
@@ -773,35 +872,67 @@ def run_e2e(args, data, ws, step_ks, dev):
             if y is not None:
                 yh = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
                 yh.copy_(y)
-            host[(dt, cond, op)] = (xh, yh, x, y)
-    bi = bo = 0
+            host[(dt, cond, op)] = (xh, yh)
+    # device buffers of their own per reduction, so that no copy refills a
+    # buffer an earlier reduction of the same step still reads
+    dbuf = {}
+    for k in step_ks:
+        xh, yh = host[k[:3]]
+        dbuf[k] = (torch.empty_like(xh, device=dev),
+                   torch.empty_like(yh, device=dev) if yh is not None else None)
+    outs = {k: torch.empty(2, dtype=torch.float32 if k[0] == "f32" else torch.float64,
+                           pin_memory=True) for k in step_ks}
+    copy_stream = torch.cuda.Stream(device=dev)
     reps = max(1, min(args.steps, 3))
 
     def one_step():
-        nonlocal bi, bo
         for k in step_ks:
             dt, cond, op, v, _ = k
-            xh, yh, xd, yd = host[(dt, cond, op)]
+            xh, yh = host[k[:3]]
+            xd, yd = dbuf[k]
             if op == "sum":
-                tf.sum_host(xh, v, x_dev=xd, ws=ws)
+                tf.sum_host_async(xh, v, x_dev=xd, ws=ws, out=outs[k], copy_stream=copy_stream)
             else:
-                tf.dot_host(xh, yh, v, x_dev=xd, y_dev=yd, ws=ws)
+                tf.dot_host_async(xh, yh, v, x_dev=xd, y_dev=yd, ws=ws, out=outs[k],
+                                  copy_stream=copy_stream)
+        torch.cuda.synchronize(dev)
+
+    def copies_only():
+        # the same host-to-device traffic with no reductions: the host link's
+        # rate at this moment, the ceiling of the end-to-end figure
+        with torch.cuda.stream(copy_stream):
+            for k in step_ks:
+                xh, yh = host[k[:3]]
+                xd, yd = dbuf[k]
+                xd.copy_(xh, non_blocking=True)
+                if yh is not None:
+                    yd.copy_(yh, non_blocking=True)
+        torch.cuda.synchronize(dev)
 
     one_step()        # warm
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
         one_step()
-    torch.cuda.synchronize()
     dt_s = (time.perf_counter() - t0) / reps
+    copies_only()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        copies_only()
+    dt_copy = (time.perf_counter() - t0) / reps
     if old_aff is not None:
         os.sched_setaffinity(0, old_aff)
     n = args.n
     step_bytes = sum(nbytes(k[0], k[2], n) for k in step_ks)
     bo = sum(16 if k[0] == "f64" else 8 for k in step_ks)
+    del dbuf
+    torch.cuda.empty_cache()
     return {"value": round(step_bytes / dt_s / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": step_bytes, "d2h_bytes_per_step": bo,
             "ms_per_step": round(dt_s * 1e3, 3), "steps": reps,
+            "link_gbs": round(step_bytes / dt_copy / 1e9, 2),
+            "e2e_over_link": round(dt_copy / dt_s, 4),
+            "calls": "tf_sum_host_async / tf_dot_host_async, copies on a second stream, "
+                     "one host wait per step",
             "host_numa_node": None if numa is None else numa[0]}
 
 
@@ -983,6 +1114,8 @@ def main(argv=None):
     ap.add_argument("--no-clocks", action="store_true", help="profiling: no nvidia-smi sampler")
     ap.add_argument("--only", default="", help="profiling: comma list of kernels, e.g. f64_dot_rigorous")
     ap.add_argument("--conds", default="1e4,1e8,1e16", help="profiling: condition numbers")
+    ap.add_argument("--split", action="store_true",
+                    help="one vector split over the ranks (shard pairs gathered and merged)")
     ap.add_argument("--layouts", action="store_true",
                     help="only the batched layout sweep (one JSON line of its own)")
     args = ap.parse_args(argv)
@@ -1000,6 +1133,12 @@ def main(argv=None):
             print(json.dumps(res))
         return 0
     import torch
+    if args.split:
+        res = run_split(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(res))
+        barrier(world)
+        return 0
     res, data, ws, outs, ks_all, step_ks = run_gpu(args, rank, world, local)
     if not args.no_batched:
         res["batched"] = run_batched(args, torch.device("cuda", local),

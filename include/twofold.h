@@ -90,7 +90,11 @@ typedef enum {
     TF_ERR_CUDA = 5,         /* a CUDA runtime call failed                        */
     TF_ERR_OFFSETS = 6,      /* device-detected: offsets not a valid CSR          */
     TF_ERR_TIMEOUT = 7,      /* a bounded wait gave up                            */
-    TF_ERR_UNSUPPORTED = 8   /* no sm_103a device, or a size beyond the limits    */
+    TF_ERR_UNSUPPORTED = 8,  /* no sm_103a device, or a size beyond the limits    */
+    TF_ERR_UNDRAINED = 9     /* device-detected: a bounded wait gave up and so did
+                                the wait for the copies still in flight; the
+                                call's results are undefined: drop its outputs
+                                and its workspace                              */
 } tf_status;
 
 /* flags */
@@ -157,6 +161,23 @@ tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtyp
                       tf_variant variant, void* out_host, void* x_dev, void* y_dev,
                       void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream);
 
+/* The same without waiting: the copies of x_host (and y_host) go on
+   copy_stream (NULL: on stream), the reduction on stream behind them (an
+   event orders it), and the pair is copied to out_host on stream; the call
+   returns once all of it is enqueued.  Wait on stream (or an event recorded
+   on it) before reading out_host or reusing any of the buffers.  Host
+   buffers should be pinned (pageable ones make the copies synchronous).  A
+   device buffer must not be refilled while an earlier call that reads it is
+   still in flight (give consecutive calls distinct x_dev / y_dev, or order
+   them).  Calls sharing ws must share stream. */
+tf_status tf_sum_host_async(const void* x_host, int64_t n, tf_dtype dtype, tf_variant variant,
+                            void* out_host, void* x_dev, void* ws, size_t ws_bytes,
+                            uint32_t flags, tf_stream_t stream, tf_stream_t copy_stream);
+tf_status tf_dot_host_async(const void* x_host, const void* y_host, int64_t n, tf_dtype dtype,
+                            tf_variant variant, void* out_host, void* x_dev, void* y_dev,
+                            void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream,
+                            tf_stream_t copy_stream);
+
 /* ---- no caller workspace ----------------------------------------------- */
 
 /* tf_sum without a caller workspace, for callers that cannot allocate device
@@ -166,15 +187,39 @@ tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtyp
    synchronization).  The paper has no counterpart: this is a deployment
    convenience.  Same kernel, launch shape and result bits as tf_sum.
    Scratch: a library-owned device array of 33,024 bytes (a 256-byte header
-   and 2048 block pairs) on every GPU that loads the library, kept until the
-   process exits; no call allocates or frees memory.  A launch shape needing
-   more than 2048 blocks returns TF_ERR_UNSUPPORTED.  The first call on a
+   and 2048 block pairs of 16 bytes) on every GPU that loads the library,
+   kept until the process exits; no call allocates or frees memory.  Every
+   launch shape fits it except for binary64 data with TF_WIDE, whose
+   binary128 pairs take 32 bytes: there a launch shape of more than 1024
+   blocks (a plan of more than 6 blocks per SM on 152 SMs) returns
+   TF_ERR_UNSUPPORTED.  The first call on a
    device looks up the array's device address (cudaGetSymbolAddress) with
    that device current; make that first call before any stream capture.
    Every call clears the array's header and shares the array, so calls that
    overlap on the GPU (other streams, other host threads) race: order them
    on one stream. */
 tf_status tf_sum_noalloc(const void* x, int64_t n, tf_dtype dtype, tf_variant variant,
+                         void* out, uint32_t flags, tf_stream_t stream);
+
+/* ---- one vector over several GPUs (or calls) --------------------------- */
+
+/* The last step of one vector cut into G contiguous shards, each reduced on
+   its own GPU (or by its own call) and the G pairs gathered in rank order
+   into one device array: merges them in rank order into the result.  The
+   paper's loops are sequential; this extends the library's merge of chain
+   pairs (TWO-SUM, Theorem 2) across shards.
+   pairs: device array of G pairs of doubles (V, E), 8-byte aligned: each
+   shard's pair as tf_sum / tf_dot write it for binary64 data, or with
+   TF_OUT_F64 for binary32 data (the binary64 cross-block pair before its
+   final rounding).  G >= 0 (0 gives (+0, +0)).
+   variant: the shards' variant (TF_DOT_LITERAL dots merge as fast /
+   rigorous).  Twofold variants (fast, rigorous, kahan): from pair 0,
+   (V, q) = TWO-SUM(V, V_g), E = (E + E_g) + q for g = 1 .. G-1, in binary64.
+   TF_PLAIN: V + V_g in the data type.  TF_WIDE: binary32 data V + V_g in
+   binary64; binary64 data S <- (S + V_g) + E_g in binary128 from S = +0.
+   out: one pair in tf_sum's output format for dtype and flags.
+   One single-thread kernel on `stream`; argument errors return before it. */
+tf_status tf_merge_pairs(const void* pairs, int64_t G, tf_dtype dtype, tf_variant variant,
                          void* out, uint32_t flags, tf_stream_t stream);
 
 /* ---- workspace --------------------------------------------------------- */
@@ -247,11 +292,12 @@ tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* 
                   int64_t n, tf_stream_t stream);
 
 /* Memory-read probe (the paper's read1/read2): streams nbytes of x (and of y
-   when not NULL) with the reductions' 128-bit streaming loads and no
-   arithmetic, 8 loads in flight per thread for one array and 4 per array for
-   two, and writes one word per block to sink (blocks words). */
+   when not NULL; nbytes a multiple of 16, both 16-byte aligned) with the
+   reductions' 128-bit streaming loads and no arithmetic, `unroll` loads of
+   each array in flight per thread (1, 2, 4 or 8), and writes one word per
+   block to sink (blocks words). */
 tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
-                        int32_t blocks, int32_t threads, tf_stream_t stream);
+                        int32_t blocks, int32_t threads, int32_t unroll, tf_stream_t stream);
 
 /* Arithmetic probe (the paper's p-functions): each thread runs `iters`
    iterations of 8 independent chains of one operation, from registers.

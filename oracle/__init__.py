@@ -10,7 +10,8 @@ ctypes wrapper over numpy arrays.
   and the dot forms)
 * ``exact``: an exact superaccumulator (the plain definition of the sum)
 * ``replay_flat`` / ``replay_csr``: the kernels' documented reduction order
-  replayed one IEEE operation at a time
+  replayed one IEEE operation at a time; ``merge_pairs``: the rank-order
+  merge of shard pairs (one vector split over several GPUs or calls)
 
 Every function here is pinned by the ``-m "not gpu"`` tests to something
 other than itself (theorems checked exhaustively on tiny formats, exact
@@ -85,6 +86,8 @@ def lib():
         L.orc_replay_csr.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, i64, C.c_int,
                                      i64, C.c_int, C.c_int, P]
         L.orc_replay_csr.restype = C.c_int
+        L.orc_merge_pairs.argtypes = [C.c_int, C.c_int, P, i64, C.c_int, P]
+        L.orc_merge_pairs.restype = C.c_int
         L.orc_default_threads.argtypes = []
         L.orc_default_threads.restype = C.c_int
         _lib = L
@@ -241,6 +244,21 @@ def replay_csr(op, variant, x, offsets, y=None, *, unroll, tile, out_f64=False, 
     if rc != 0:
         raise ValueError("orc_replay_csr: bad arguments")
     return out[:nseg]
+
+
+def merge_pairs(pairs, dtype, variant, out_f64=False):
+    """Merge G shard pairs (a (G, 2) binary64 array: each shard's pair as a
+    binary32 call with the binary64 output, or a binary64 call, writes it) in
+    rank order; returns the output pair in the reductions' output format."""
+    pr = _c(np.asarray(pairs, dtype=np.float64).reshape(-1, 2))
+    code = F32 if np.dtype(dtype) == np.float32 else F64
+    odt = np.float64 if (code == F64 or out_f64) else np.float32
+    out = np.zeros(2, dtype=odt)
+    rc = lib().orc_merge_pairs(code, VARIANTS[variant], _ptr(pr), pr.shape[0], int(bool(out_f64)),
+                               _ptr(out))
+    if rc != 0:
+        raise ValueError("orc_merge_pairs: bad arguments")
+    return out
 
 
 def default_threads():

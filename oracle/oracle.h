@@ -111,6 +111,10 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
 int orc_replay_csr(int dtype, int op, int variant, const void* x, const void* y,
                    const int64_t* off, int64_t nseg, int unroll, int64_t tile,
                    int out_f64, int nthreads, void* out);
+/* merge of G shard pairs (binary64 (V, E) each) in rank order, output as the
+   reductions write theirs (see replay.c) */
+int orc_merge_pairs(int dtype, int variant, const double* pairs, int64_t G, int out_f64,
+                    void* out);
 
 #ifdef __cplusplus
 }

@@ -377,3 +377,38 @@ int orc_replay_csr(int dtype, int op, int variant, const void* x, const void* y,
     free(th);
     return 0;
 }
+
+/* ----------------------------------------------------------- rank merge */
+/* Merge G shard pairs in rank order: the last step of one vector cut into G
+   contiguous shards, each reduced on its own (one GPU or one call each).
+   pairs holds G binary64 pairs (V, E): each shard's cross-block pair, for
+   binary32 data its binary64 output form.  Twofold variants (fast, rigorous,
+   kahan, the literal dots): from pair 0, pair <- merge(pair, pair g) for
+   g = 1 .. G-1 with the TWO-SUM merge above, in binary64.  Plain: V + V_g
+   in the data type.  Wide: binary32 data V + V_g in binary64; binary64 data
+   S <- (S + V_g) + E_g in binary128 from S = +0, output (RN64(S),
+   RN64(S - RN64(S))).  G = 0 gives (+0, +0).  Output as write_out above. */
+int orc_merge_pairs(int dtype, int variant, const double* pairs, int64_t G, int out_f64,
+                    void* out) {
+    if ((dtype != ORC_F32 && dtype != ORC_F64) || variant < 0 || variant > 6 || G < 0 ||
+        (G > 0 && !pairs) || !out)
+        return -1;
+    prob_t P = { dtype, 0, variant, NULL, NULL };
+    pr_t r = { 0.0, 0.0, 0 };
+    if (dtype == ORC_F64 && variant == 3) {
+        _Float128 S = 0;
+        for (int64_t g = 0; g < G; ++g)
+            S = (S + (_Float128)pairs[2 * g]) + (_Float128)pairs[2 * g + 1];
+        r.q = S;
+    } else if (G > 0) {
+        const int f = f_grid(&P), tw = twofold(&P);
+        r.s = pairs[0];
+        r.e = pairs[1];
+        for (int64_t g = 1; g < G; ++g) {
+            pr_t b = { pairs[2 * g], pairs[2 * g + 1], 0 };
+            r = merge(f, tw, r, b);
+        }
+    }
+    write_out(&P, r, out_f64, out);
+    return 0;
+}

@@ -219,6 +219,7 @@ const char* tf_status_string(tf_status s) {
     case TF_ERR_OFFSETS: return "invalid CSR offsets";
     case TF_ERR_TIMEOUT: return "bounded wait timed out";
     case TF_ERR_UNSUPPORTED: return "unsupported device or size";
+    case TF_ERR_UNDRAINED: return "bounded wait timed out with copies still in flight";
     }
     return "unknown status";
 }
@@ -299,6 +300,62 @@ tf_status tf_dot_host(const void* x_host, const void* y_host, int64_t n, tf_dtyp
     Range r("tf_dot_host");
     return host_call(1, x_host, y_host, n, dtype, variant, out_host, x_dev, y_dev, ws, ws_bytes,
                      flags, (cudaStream_t)stream);
+}
+
+// The asynchronous form: copies on `cs` (or on `st` when cs is NULL or st),
+// the reduction on `st` ordered behind them by an event, the pair copied back
+// on `st`; nothing waits.
+static tf_status host_call_async(int op, const void* xh, const void* yh, int64_t n, int dtype,
+                                 int variant, void* out_host, void* xd, void* yd, void* ws,
+                                 size_t ws_bytes, uint32_t flags, cudaStream_t st,
+                                 cudaStream_t cs) {
+    if (!out_host || (n > 0 && (!xh || !xd || (op == 1 && (!yh || !yd))))) return TF_ERR_ARG;
+    if (n < 0) return TF_ERR_ARG;
+    if (!ws) return TF_ERR_ARG;
+    void* stage = (char*)ws + kStageOffset;
+    tf_status s = common_checks(op, dtype, variant, xd, yd, n, stage, ws, ws_bytes);
+    if (s != TF_OK) return s;
+    if (ws_bytes < flat_ws_bytes()) return TF_ERR_WORKSPACE;
+    int sms = 0;
+    if ((s = check_device(&sms)) != TF_OK) return s;
+    const bool two = cs != nullptr && cs != st;
+    const size_t bytes = (size_t)n * esize(dtype);
+    cudaStream_t c = two ? cs : st;
+    if (n > 0) {
+        if (cudaMemcpyAsync(xd, xh, bytes, cudaMemcpyHostToDevice, c) != cudaSuccess) return TF_ERR_CUDA;
+        if (op == 1 && cudaMemcpyAsync(yd, yh, bytes, cudaMemcpyHostToDevice, c) != cudaSuccess)
+            return TF_ERR_CUDA;
+    }
+    if (two) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return TF_ERR_CUDA;
+        const bool ok = cudaEventRecord(ev, cs) == cudaSuccess &&
+                        cudaStreamWaitEvent(st, ev, 0) == cudaSuccess;
+        cudaEventDestroy(ev);              // released once the wait is satisfied
+        if (!ok) return TF_ERR_CUDA;
+    }
+    s = run_flat(op, xd, yd, n, dtype, variant, stage, ws, ws_bytes, flags, st);
+    if (s != TF_OK) return s;
+    const size_t ob = (dtype == TF_F64 || (flags & TF_OUT_F64)) ? 16 : 8;
+    if (cudaMemcpyAsync(out_host, stage, ob, cudaMemcpyDeviceToHost, st) != cudaSuccess) return TF_ERR_CUDA;
+    return TF_OK;
+}
+
+tf_status tf_sum_host_async(const void* x_host, int64_t n, tf_dtype dtype, tf_variant variant,
+                            void* out_host, void* x_dev, void* ws, size_t ws_bytes,
+                            uint32_t flags, tf_stream_t stream, tf_stream_t copy_stream) {
+    Range r("tf_sum_host_async");
+    return host_call_async(0, x_host, nullptr, n, dtype, variant, out_host, x_dev, nullptr, ws,
+                           ws_bytes, flags, (cudaStream_t)stream, (cudaStream_t)copy_stream);
+}
+
+tf_status tf_dot_host_async(const void* x_host, const void* y_host, int64_t n, tf_dtype dtype,
+                            tf_variant variant, void* out_host, void* x_dev, void* y_dev,
+                            void* ws, size_t ws_bytes, uint32_t flags, tf_stream_t stream,
+                            tf_stream_t copy_stream) {
+    Range r("tf_dot_host_async");
+    return host_call_async(1, x_host, y_host, n, dtype, variant, out_host, x_dev, y_dev, ws,
+                           ws_bytes, flags, (cudaStream_t)stream, (cudaStream_t)copy_stream);
 }
 
 tf_status tf_workspace_size(tf_op op, int batched, tf_dtype dtype, tf_variant variant,
@@ -471,6 +528,23 @@ tf_status tf_plan_load(const char* path) {
     return TF_OK;
 }
 
+tf_status tf_merge_pairs(const void* pairs, int64_t G, tf_dtype dtype, tf_variant variant,
+                         void* out, uint32_t flags, tf_stream_t stream) {
+    Range r("tf_merge_pairs");
+    if (G < 0 || G > ((int64_t)1 << 30) || !out || (G > 0 && !pairs) || variant < 0 ||
+        variant >= kVariants)
+        return TF_ERR_ARG;
+    if (dtype != TF_F32 && dtype != TF_F64) return TF_ERR_DTYPE;
+    const uintptr_t oes = (dtype == TF_F64 || (flags & TF_OUT_F64)) ? 8 : 4;
+    if ((uintptr_t)pairs % 8 || (uintptr_t)out % oes) return TF_ERR_ALIGN;
+    int sms = 0;
+    tf_status s = check_device(&sms);
+    if (s != TF_OK) return s;
+    return tf::launch_merge_pairs((const double*)pairs, G, dtype, variant, out,
+                                  (flags & TF_OUT_F64) ? 1 : 0, (cudaStream_t)stream) == cudaSuccess
+               ? TF_OK : TF_ERR_CUDA;
+}
+
 tf_status tf_count_large_errors(const void* pairs, int64_t npairs, tf_dtype pair_dtype,
                                 double tau, int32_t* count, tf_stream_t stream) {
     if (npairs < 0 || !count || (npairs > 0 && !pairs) || !(tau >= 0.0)) return TF_ERR_ARG;
@@ -495,14 +569,15 @@ tf_status tf_prim(int prim, tf_dtype dtype, const void* a, const void* b, void* 
 }
 
 tf_status tf_probe_read(const void* x, const void* y, int64_t nbytes, void* sink, int32_t blocks,
-                        int32_t threads, tf_stream_t stream) {
-    if (!x || !sink || nbytes < 0 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32)
+                        int32_t threads, int32_t unroll, tf_stream_t stream) {
+    if (!x || !sink || nbytes < 0 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32 ||
+        (unroll != 1 && unroll != 2 && unroll != 4 && unroll != 8))
         return TF_ERR_ARG;
     if ((uintptr_t)x % 16 || (y && (uintptr_t)y % 16) || nbytes % 16) return TF_ERR_ALIGN;
     int sms = 0;
     tf_status s = check_device(&sms);
     if (s != TF_OK) return s;
-    return tf::launch_probe_read(x, y, nbytes, sink, blocks, threads, (cudaStream_t)stream) ==
+    return tf::launch_probe_read(x, y, nbytes, sink, blocks, threads, unroll, (cudaStream_t)stream) ==
                    cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
 

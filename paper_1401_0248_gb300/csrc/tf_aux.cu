@@ -7,6 +7,8 @@
 //                 reductions' 128-bit loads and no arithmetic.
 //   alu_probe     the paper's p-functions: the per-item operations from
 //                 registers, 8 independent chains per thread, no loads.
+//   merge_pairs_kernel  the rank-order merge of shard pairs (one vector
+//                 reduced in contiguous shards, one per GPU or call).
 #include "tf_async.cuh"
 #include "tf_device.cuh"
 #include "tf_internal.h"
@@ -87,10 +89,54 @@ cudaError_t launch_large_errors(const void* pairs, int64_t npairs, int dtype, do
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- rank merge
+// G shard pairs (binary64 (V, E) each: a shard's cross-block pair, as a
+// binary32 call writes it with TF_OUT_F64 or a binary64 call writes it)
+// merged in rank order by one thread, in the precision of the grid fold:
+// the twofold variants by the TWO-SUM merge, plain and wide by one addition;
+// the binary128 accumulator ('wide' binary64) as S <- (S + V_g) + E_g.
+template <typename T, int VAR>
+__global__ void merge_pairs_kernel(const double* __restrict__ pairs, int64_t G,
+                                   void* __restrict__ out, int out_f64) {
+    using Gt = typename GridAcc<T, VAR>::type;
+    constexpr bool TW = twofold_v<VAR>;
+    if (threadIdx.x != 0) return;
+    if constexpr (sizeof(Gt) == 16) {
+        q128 S(0);
+        for (int64_t g = 0; g < G; ++g)
+            S = q_add(q_add(S, q128(pairs[2 * g])), q128(pairs[2 * g + 1]));
+        write_out<T, VAR, q128>(out, 0, S, q128(0), false);
+    } else {
+        Gt V = Gt(0), E = Gt(0);
+        if (G > 0) { V = (Gt)pairs[0]; E = (Gt)pairs[1]; }
+        for (int64_t g = 1; g < G; ++g) merge<TW>(V, E, (Gt)pairs[2 * g], (Gt)pairs[2 * g + 1]);
+        write_out<T, VAR, Gt>(out, 0, V, E, out_f64 != 0);
+    }
+}
+
+template <typename T>
+static void launch_merge_t(int variant, const double* pairs, int64_t G, void* out, int out_f64,
+                           cudaStream_t st) {
+    switch (variant) {
+    case PLAIN: merge_pairs_kernel<T, PLAIN><<<1, 32, 0, st>>>(pairs, G, out, out_f64); break;
+    case FAST: merge_pairs_kernel<T, FAST><<<1, 32, 0, st>>>(pairs, G, out, out_f64); break;
+    case RIGOROUS: merge_pairs_kernel<T, RIGOROUS><<<1, 32, 0, st>>>(pairs, G, out, out_f64); break;
+    case WIDE: merge_pairs_kernel<T, WIDE><<<1, 32, 0, st>>>(pairs, G, out, out_f64); break;
+    default: merge_pairs_kernel<T, KAHAN><<<1, 32, 0, st>>>(pairs, G, out, out_f64); break;
+    }
+}
+
+cudaError_t launch_merge_pairs(const double* pairs, int64_t G, int dtype, int variant, void* out,
+                               int out_f64, cudaStream_t st) {
+    if (dtype == 0) launch_merge_t<float>(variant, pairs, G, out, out_f64, st);
+    else launch_merge_t<double>(variant, pairs, G, out, out_f64, st);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ read probe
-// U 16-byte loads of each array in flight per thread and step: one array
-// takes 8 (128 bytes), two arrays 4 each, so that either form keeps as many
-// bytes in flight per thread as the reductions' best plans.
+// U 16-byte loads of each array in flight per thread and step (U = 1, 2, 4
+// or 8); the caller picks U and the launch shape, and a sweep over them gives
+// the best streaming read rate of one or two arrays.
 template <int U, bool TWO>
 __global__ void __launch_bounds__(1024)
 read_probe(const float* __restrict__ x, const float* __restrict__ y, int64_t nvec,
@@ -135,14 +181,27 @@ read_probe(const float* __restrict__ x, const float* __restrict__ y, int64_t nve
     }
 }
 
-cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
-                              int blocks, int threads, cudaStream_t st) {
+template <int U>
+static void launch_read_u(const void* x, const void* y, int64_t nvec, void* sink, int blocks,
+                          int threads, cudaStream_t st) {
     if (y)
-        read_probe<4, true><<<blocks, threads, 0, st>>>((const float*)x, (const float*)y,
-                                                        nbytes / 16, (unsigned int*)sink);
+        read_probe<U, true><<<blocks, threads, 0, st>>>((const float*)x, (const float*)y, nvec,
+                                                        (unsigned int*)sink);
     else
-        read_probe<8, false><<<blocks, threads, 0, st>>>((const float*)x, nullptr, nbytes / 16,
+        read_probe<U, false><<<blocks, threads, 0, st>>>((const float*)x, nullptr, nvec,
                                                          (unsigned int*)sink);
+}
+
+cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
+                              int blocks, int threads, int unroll, cudaStream_t st) {
+    const int64_t nvec = nbytes / 16;
+    switch (unroll) {
+    case 1: launch_read_u<1>(x, y, nvec, sink, blocks, threads, st); break;
+    case 2: launch_read_u<2>(x, y, nvec, sink, blocks, threads, st); break;
+    case 4: launch_read_u<4>(x, y, nvec, sink, blocks, threads, st); break;
+    case 8: launch_read_u<8>(x, y, nvec, sink, blocks, threads, st); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@
 // 16/sizeof(T)) are read from global memory directly.  Every wait is bounded;
 // a wait that gives up sets TF_ERR_TIMEOUT in the workspace's error word,
 // waits (bounded again) for the warp's copies in flight and ends the warp's
-// work.
+// work; if that wait gives up as well the error word becomes
+// TF_ERR_UNDRAINED (copies may land after the block exits).
 #include "tf_async.cuh"
 #include "tf_csr.cuh"
 
@@ -33,6 +34,7 @@ constexpr int kChunkBytes = kRows * kRowBytes;  // 4 KiB per operand
 constexpr int kStages = 3;
 constexpr int kMaxWarps = 16;
 constexpr int kTfErrTimeout = 7;               // TF_ERR_TIMEOUT
+constexpr int kTfErrUndrained = 9;             // TF_ERR_UNDRAINED
 constexpr unsigned kWaitLimit = 1u << 20;      // try_wait rounds before giving up
 
 
@@ -263,8 +265,15 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
         }
         if (failed) {
             if (lane == 0) atomicExch(&hdr->error, kTfErrTimeout);
-            // let the copies still in flight land before the block can exit
-            for (uint32_t k = freed; k < issued; ++k) mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u, kWaitLimit);
+            // let the copies still in flight land before the block can exit;
+            // if one of these bounded waits gives up too, copies may still be
+            // landing in this block's shared memory after it exits: that is
+            // recorded as its own status (the results of the call are then
+            // undefined and the workspace should be dropped)
+            bool drained = true;
+            for (uint32_t k = freed; k < issued; ++k)
+                drained = mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u, kWaitLimit) && drained;
+            if (!drained && lane == 0) atomicExch(&hdr->error, kTfErrUndrained);
         }
     }
 

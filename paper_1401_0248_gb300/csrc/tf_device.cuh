@@ -94,8 +94,8 @@ __device__ __forceinline__ void two_product(T a, T b, T& p, T& e) {
 }
 
 // ---- hybrid binary64 transforms: x from one binary64 add, the error on the
-// integer pipe.  GB300's integer ALU pipe, not its binary64 pipe, limits the
-// all-integer TWO-SUM above; this split keeps both pipes busy.
+// integer pipe.  A TWO-SUM done wholly in integers (rounding included) is
+// limited by GB300's integer ALU pipe; this split keeps both pipes busy.
 //
 // The error of x = RN(a + b) in units of 2^(emin - 1075), emin the smaller
 // exponent field: r = ma*2^(ea-emin) +- mb*2^(eb-emin) -+ mx*2^(ex-emin).

@@ -37,10 +37,12 @@ cudaError_t launch_csr_tma(int dtype, int variant, int dot, int unroll, const vo
 
 cudaError_t launch_prim(int prim, int dtype, const void* a, const void* b, void* x, void* y,
                         int64_t n, cudaStream_t st);
+cudaError_t launch_merge_pairs(const double* pairs, int64_t G, int dtype, int variant, void* out,
+                               int out_f64, cudaStream_t st);
 cudaError_t launch_large_errors(const void* pairs, int64_t npairs, int dtype, double tau,
                                 int* count, cudaStream_t st);
 cudaError_t launch_probe_read(const void* x, const void* y, int64_t nbytes, void* sink,
-                              int blocks, int threads, cudaStream_t st);
+                              int blocks, int threads, int unroll, cudaStream_t st);
 cudaError_t launch_probe_alu(int kind, int64_t iters, void* sink, int blocks, int threads,
                              cudaStream_t st);
 cudaError_t launch_probe_wait(int arrive, int64_t polls, int* flag, cudaStream_t st);

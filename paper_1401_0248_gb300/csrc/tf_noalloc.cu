@@ -65,8 +65,12 @@ extern "C" tf_status tf_sum_noalloc(const void* x, int64_t n, tf_dtype dtype,
     int64_t grid = 0, tile = 0;
     tf_status s = tf_launch_shape(TF_OP_SUM, 0, dtype, variant, n, &block, &unroll, &grid, &tile);
     if (s != TF_OK) return s;
-    if (grid > kNoallocMaxBlocks) return TF_ERR_UNSUPPORTED;   // scratch holds 2048 blocks
-    // a binary128 accumulator ('wide' binary64) needs two 16-byte slots per block
+    // every launch shape tf_launch_shape gives has at most kMaxFlatGrid blocks
+    // of 16-byte pairs, which the array holds; a binary128 accumulator
+    // ('wide' binary64) takes two 16-byte slots per block, so those calls
+    // are limited to half as many blocks (a plan of more than 1024 blocks
+    // for that key, e.g. 8 blocks per SM on 152 SMs, is rejected)
+    static_assert(tf::kMaxFlatGrid <= kNoallocMaxBlocks, "scratch array below the largest grid");
     if (dtype == TF_F64 && variant == TF_WIDE && grid > kNoallocMaxBlocks / 2) return TF_ERR_UNSUPPORTED;
 
     void* scratch = nullptr;

@@ -42,7 +42,7 @@ def plan_class(n, batched=False):
 
 STATUS = {0: "TF_OK", 1: "TF_ERR_ARG", 2: "TF_ERR_DTYPE", 3: "TF_ERR_WORKSPACE",
           4: "TF_ERR_ALIGN", 5: "TF_ERR_CUDA", 6: "TF_ERR_OFFSETS", 7: "TF_ERR_TIMEOUT",
-          8: "TF_ERR_UNSUPPORTED"}
+          8: "TF_ERR_UNSUPPORTED", 9: "TF_ERR_UNDRAINED"}
 
 # every symbol declared in include/twofold.h, with its ctypes signature
 _P, _I64, _I32, _SZ, _U32 = C.c_void_p, C.c_int64, C.c_int32, C.c_size_t, C.c_uint32
@@ -51,6 +51,9 @@ SIGNATURES = {
     "tf_dot": ([_P, _P, _I64, C.c_int, C.c_int, _P, _P, _SZ, _U32, _P], C.c_int),
     "tf_sum_batched": ([_P, _I64, _P, _I64, C.c_int, C.c_int, _P, _P, _SZ, _U32, _P], C.c_int),
     "tf_dot_batched": ([_P, _P, _I64, _P, _I64, C.c_int, C.c_int, _P, _P, _SZ, _U32, _P], C.c_int),
+    "tf_sum_host_async": ([_P, _I64, C.c_int, C.c_int, _P, _P, _P, _SZ, _U32, _P, _P], C.c_int),
+    "tf_dot_host_async": ([_P, _P, _I64, C.c_int, C.c_int, _P, _P, _P, _P, _SZ, _U32, _P, _P],
+                          C.c_int),
     "tf_sum_host": ([_P, _I64, C.c_int, C.c_int, _P, _P, _P, _SZ, _U32, _P], C.c_int),
     "tf_sum_noalloc": ([_P, _I64, C.c_int, C.c_int, _P, _U32, _P], C.c_int),
     "tf_dot_host": ([_P, _P, _I64, C.c_int, C.c_int, _P, _P, _P, _P, _SZ, _U32, _P], C.c_int),
@@ -66,8 +69,9 @@ SIGNATURES = {
     "tf_plan_save": ([C.c_char_p], C.c_int),
     "tf_plan_load": ([C.c_char_p], C.c_int),
     "tf_prim": ([C.c_int, C.c_int, _P, _P, _P, _P, _I64, _P], C.c_int),
+    "tf_merge_pairs": ([_P, _I64, C.c_int, C.c_int, _P, _U32, _P], C.c_int),
     "tf_count_large_errors": ([_P, _I64, C.c_int, C.c_double, _P, _P], C.c_int),
-    "tf_probe_read": ([_P, _P, _I64, _P, _I32, _I32, _P], C.c_int),
+    "tf_probe_read": ([_P, _P, _I64, _P, _I32, _I32, _I32, _P], C.c_int),
     "tf_probe_alu": ([C.c_int, _I64, _P, _I32, _I32, _P], C.c_int),
     "tf_probe_wait": ([_I32, _I64, _P, _P], C.c_int),
     "tf_status_string": ([C.c_int], C.c_char_p),
@@ -260,6 +264,37 @@ def dot_batched(x, y, offsets, variant="fast", *, out_f64=False, out=None, ws=No
     return out
 
 
+def shard_bounds(n, G, dtype=torch.float32):
+    """Contiguous shards of one vector of n elements for G GPUs (or calls):
+    shard g is [g*m, min((g+1)*m, n)) with m = ceil(n / (G*V)) * V elements,
+    V = 16 / element size, so that every shard starts on a 16-byte boundary
+    of a 16-byte-aligned vector (the last shards may be short or empty)."""
+    if G < 1 or n < 0:
+        raise ValueError("G >= 1 and n >= 0")
+    V = 4 if dtype == torch.float32 else 2
+    m = -(-n // (G * V)) * V
+    return [(min(g * m, n), min((g + 1) * m, n)) for g in range(G)]
+
+
+def merge_pairs(pairs, dtype, variant="fast", *, out_f64=False, out=None):
+    """Merge the (G, 2) binary64 device tensor of shard pairs (rank order) of
+    one vector reduced in G contiguous shards into one pair (tf_merge_pairs);
+    dtype is the data's dtype (binary32 shards give their pairs with
+    out_f64=True)."""
+    if pairs.dtype != torch.float64 or pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must be a (G, 2) float64 tensor")
+    if not pairs.is_cuda:
+        raise ValueError("pairs must be a CUDA tensor")
+    pairs = pairs.contiguous()
+    odt = torch.float64 if (dtype == torch.float64 or out_f64) else torch.float32
+    if out is None:
+        out = torch.empty(2, dtype=odt, device=pairs.device)
+    _check("tf_merge_pairs", lib().tf_merge_pairs(_ptr(pairs), pairs.shape[0], DTYPES[dtype],
+                                                  VARIANTS[variant], _ptr(out),
+                                                  OUT_F64 if out_f64 else 0, _stream(pairs)))
+    return out
+
+
 def count_large_errors(pairs, tau, count=None):
     """Number of pairs (value, error) with |error| > tau * |value| (or not
     finite), as a device int32 tensor; pairs is an (n, 2) or (2,) tensor."""
@@ -320,6 +355,52 @@ def dot_host(x, y, variant="fast", *, out_f64=False, x_dev=None, y_dev=None, ws=
                            OUT_F64 if out_f64 else 0, _stream(x_dev))
     _check("tf_dot_host", rc)
     return res[0], res[1]
+
+
+def _host_out(x, out_f64, out):
+    odt = torch.float64 if (x.dtype == torch.float64 or out_f64) else torch.float32
+    if out is None:
+        out = torch.empty(2, dtype=odt, pin_memory=True)
+    if out.is_cuda or out.dtype != odt or out.numel() != 2 or not out.is_contiguous():
+        raise ValueError("out: a contiguous CPU tensor of two %s expected" % odt)
+    return out
+
+
+def sum_host_async(x, variant="fast", *, x_dev, ws, out=None, out_f64=False, copy_stream=None):
+    """Enqueue a twofold sum of host data without waiting (tf_sum_host_async):
+    x (pinned, 1-D) is copied to x_dev on copy_stream (default: the current
+    stream of x_dev's device), the reduction runs on the current stream
+    behind the copy, and the pair lands in `out` (a pinned CPU tensor,
+    returned) once that stream reaches it."""
+    if x.is_cuda or x.dim() != 1 or not x.is_contiguous():
+        raise ValueError("sum_host_async: a 1-D contiguous CPU tensor expected")
+    if x_dev.dtype != x.dtype or x_dev.numel() != x.numel() or not x_dev.is_cuda:
+        raise ValueError("x_dev: a CUDA tensor of x's dtype and size expected")
+    out = _host_out(x, out_f64, out)
+    cs = None if copy_stream is None else C.c_void_p(copy_stream.cuda_stream)
+    _check("tf_sum_host_async",
+           lib().tf_sum_host_async(_ptr(x), x.numel(), _dt(x), VARIANTS[variant], _ptr(out),
+                                   _ptr(x_dev), _ptr(ws), ws.numel(), OUT_F64 if out_f64 else 0,
+                                   _stream(x_dev), cs))
+    return out
+
+
+def dot_host_async(x, y, variant="fast", *, x_dev, y_dev, ws, out=None, out_f64=False,
+                   copy_stream=None):
+    """The dot-product form of sum_host_async."""
+    if (x.is_cuda or y.is_cuda or x.dtype != y.dtype or x.numel() != y.numel() or x.dim() != 1
+            or y.dim() != 1 or not x.is_contiguous() or not y.is_contiguous()):
+        raise ValueError("dot_host_async: two matching 1-D contiguous CPU tensors expected")
+    for d in (x_dev, y_dev):
+        if d.dtype != x.dtype or d.numel() != x.numel() or not d.is_cuda:
+            raise ValueError("x_dev, y_dev: CUDA tensors of x's dtype and size expected")
+    out = _host_out(x, out_f64, out)
+    cs = None if copy_stream is None else C.c_void_p(copy_stream.cuda_stream)
+    _check("tf_dot_host_async",
+           lib().tf_dot_host_async(_ptr(x), _ptr(y), x.numel(), _dt(x), VARIANTS[variant],
+                                   _ptr(out), _ptr(x_dev), _ptr(y_dev), _ptr(ws), ws.numel(),
+                                   OUT_F64 if out_f64 else 0, _stream(x_dev), cs))
+    return out
 
 
 # ------------------------------------------------------------------- plans
@@ -387,14 +468,15 @@ def prim(name, a, b):
     return x, y
 
 
-def probe_read(x, y=None, blocks=None, threads=512, sink=None):
-    """Launch the read-bandwidth probe over x (and y) once."""
+def probe_read(x, y=None, blocks=None, threads=512, unroll=4, sink=None):
+    """Launch the read-bandwidth probe over x (and y) once, `unroll` 16-byte
+    loads of each array in flight per thread."""
     blocks = blocks or 4 * sm_count()
     if sink is None:
         sink = torch.empty(blocks, dtype=torch.int32, device=x.device)
     nbytes = x.numel() * x.element_size()
     _check("tf_probe_read", lib().tf_probe_read(_ptr(x), _ptr(y), nbytes, _ptr(sink), blocks, threads,
-                                                _stream(x)))
+                                                unroll, _stream(x)))
     return sink
 
 

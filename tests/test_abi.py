@@ -47,6 +47,7 @@ def test_host_side_checks_without_gpu():
     L = twofold.lib()
     assert twofold.status_string(0) == "ok"
     assert twofold.status_string(6) == "invalid CSR offsets"
+    assert "in flight" in twofold.status_string(9)
     b = C.c_size_t(0)
     assert L.tf_workspace_size(0, 0, 0, 1, 1 << 20, 0, C.byref(b)) == 0 and b.value > 256
     assert L.tf_workspace_size(0, 1, 0, 1, 1 << 20, 100, C.byref(b)) == 0
@@ -125,3 +126,15 @@ def test_product_path_has_no_cpu_fallback():
         twofold.sum(torch.zeros(10))
     src = open(os.path.join(ROOT, "paper_1401_0248_gb300", "twofold.py")).read()
     assert "oracle" not in src.replace("oracle is", "")
+
+
+def test_build_rebuilds_on_every_header():
+    """Every header of csrc/ and include/ (the batched kernels' tf_csr.cuh and
+    tf_async.cuh included) is a dependency of every object, so an edit to any
+    of them rebuilds the library."""
+    csrc = os.path.join(ROOT, "paper_1401_0248_gb300", "csrc")
+    deps = set(os.path.basename(h) for h in libbuild._headers())
+    for f in os.listdir(csrc):
+        if f.endswith((".cuh", ".h")):
+            assert f in deps, f
+    assert {"tf_csr.cuh", "tf_async.cuh", "twofold.h"} <= deps

@@ -661,6 +661,31 @@ def test_host_buffer_calls_match_device_calls():
         assert (v, e) == (d[0], d[1])
 
 
+def test_host_async_calls_match_device_calls():
+    """The asynchronous host-buffer calls, several in flight at once (copies
+    on a second stream, or on the compute stream), give the device calls'
+    bits once the stream is synchronized."""
+    n = (1 << 20) + 3
+    cs = torch.cuda.Stream()
+    for copy_stream in (cs, None):
+        calls = []
+        for k, dt in enumerate(("f32", "f64", "f32")):
+            x = I.normal(n, dt, seed=50 + k).pin_memory()
+            y = I.normal(n, dt, seed=50 + k, stream=1).pin_memory()
+            ws = tf.workspace(tf.workspace_size("dot", False, x.dtype, "rigorous", n), DEV)
+            xd, yd = torch.empty_like(x, device=DEV), torch.empty_like(y, device=DEV)
+            xs = torch.empty_like(x, device=DEV)
+            o1 = tf.sum_host_async(x, "rigorous", x_dev=xs, ws=ws, copy_stream=copy_stream)
+            o2 = tf.dot_host_async(x, y, "fast", x_dev=xd, y_dev=yd, ws=ws, out_f64=True,
+                                   copy_stream=copy_stream)
+            calls.append((x, y, o1, o2))
+        torch.cuda.synchronize()
+        for x, y, o1, o2 in calls:
+            d1 = _np(tf.sum(x.to(DEV), "rigorous"))
+            d2 = _np(tf.dot(x.to(DEV), y.to(DEV), "fast", out_f64=True))
+            assert same_bits(o1.numpy(), d1) and same_bits(o2.numpy(), d2)
+
+
 @pytest.mark.parametrize("n", [1 << 20, (1 << 22) + 1])
 def test_tuner_picks_a_valid_plan_and_stays_exact(n):
     """tf_tune stores its choice in the plan class of n (small or large)."""
@@ -681,8 +706,11 @@ def test_tuner_picks_a_valid_plan_and_stays_exact(n):
 
 def test_probes_run():
     x = torch.zeros(1 << 24, device=DEV)
-    tf.probe_read(x)
-    tf.probe_read(x, x)
+    for unroll in (1, 2, 4, 8):
+        tf.probe_read(x, unroll=unroll)
+        tf.probe_read(x, x, unroll=unroll)
+    with pytest.raises(tf.TwofoldError):
+        tf.probe_read(x, unroll=3)
     for k in tf.ALU_KINDS:
         tf.probe_alu(k, 100, 152, 256, device=DEV)
     torch.cuda.synchronize()

@@ -1,7 +1,8 @@
 """Multi-rank logic on CPU (no GPU): the benchmark's aggregation over ranks
 with a world_size-2 gloo process group, and the shard-and-merge reading of
 the method (each rank reduces its own contiguous shard to a pair; the pairs
-merge by TWO-SUM in fixed rank order), emulated with the oracle.
+are all-gathered and merge by TWO-SUM in fixed rank order), with the shard
+pairs computed by the oracle and gathered by the benchmark's own gather.
 
 The path shards into independent problems, so bench.py --gpus N runs one
 problem per rank with no collective on the data path; the only cross-rank
@@ -57,6 +58,74 @@ def test_bench_aggregation_over_two_gloo_ranks():
     for rank, mx, tot in got:
         assert mx == 17.25          # the slowest rank's step time
         assert tot == 3000.0        # bytes of all ranks
+
+
+def _split_rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank), TF_BENCH_BACKEND="gloo")
+    import torch
+    import bench
+    from paper_1401_0248_gb300 import twofold as tf
+    r, w, _ = bench.dist_setup()
+    out = {}
+    for dt, variant in (("f64", "rigorous"), ("f32", "fast"), ("f64", "wide")):
+        n = 100003
+        x = I.normal(n, dt, seed=60).numpy()
+        a, b = tf.shard_bounds(n, w, torch.float32 if dt == "f32" else torch.float64)[r]
+        mine = O.replay_flat("sum", variant, x[a:b], block=128, unroll=2, grid=5,
+                             out_f64=(dt == "f32")).astype(np.float64)
+        allp = bench.gather_pairs(torch.from_numpy(mine), w)
+        assert tuple(allp.shape) == (w, 2)
+        out[(dt, variant)] = (allp.numpy().copy(),
+                              O.merge_pairs(allp.numpy(), np.float32 if dt == "f32" else np.float64,
+                                            variant))
+    bench.barrier(w)
+    q.put((r, out))
+    dist.destroy_process_group()
+
+
+def test_split_gather_and_merge_over_two_gloo_ranks():
+    """Each rank's shard pair, gathered with the benchmark's all-gather, lands
+    in rank order on both ranks, and both merge to the same pair as one
+    process merging the two shard pairs itself."""
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_split_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    for dt, variant in (("f64", "rigorous"), ("f32", "fast"), ("f64", "wide")):
+        n = 100003
+        x = I.normal(n, dt, seed=60).numpy()
+        td = torch.float32 if dt == "f32" else torch.float64
+        want_pairs = np.array([O.replay_flat("sum", variant, x[a:b], block=128, unroll=2, grid=5,
+                                             out_f64=(dt == "f32")).astype(np.float64)
+                               for a, b in tf.shard_bounds(n, 2, td)])
+        want = O.merge_pairs(want_pairs, np.float32 if dt == "f32" else np.float64, variant)
+        for r in (0, 1):
+            pairs, merged = got[r][(dt, variant)]
+            assert np.array_equal(pairs.view(np.uint8), want_pairs.view(np.uint8))
+            assert np.array_equal(merged.view(np.uint8), want.view(np.uint8))
+
+
+def test_shard_bounds():
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+    for n in (0, 1, 7, 100003, 1 << 20):
+        for G in (1, 2, 3, 8):
+            for td, V in ((torch.float32, 4), (torch.float64, 2)):
+                sb = tf.shard_bounds(n, G, td)
+                assert len(sb) == G and sb[0][0] == 0 and sb[-1][1] == n
+                for (a, b), (c, d) in zip(sb, sb[1:]):
+                    assert b == c
+                for a, b in sb:
+                    assert a <= b and (a % V == 0 or a == n)
 
 
 def test_reference_arm_other_ranks_exit_without_work(monkeypatch):

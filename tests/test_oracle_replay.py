@@ -451,3 +451,80 @@ def test_replay_csr_binary128_matches_composition():
         want.append(out_q(res))
     got = O.replay_csr("sum", "wide", x, off, unroll=unroll, tile=tile)
     assert np.array_equal(got.view(np.uint8), np.array(want).view(np.uint8))
+
+
+# ------------------------------------------------------------- rank merge
+def test_merge_pairs_pinned_to_two_sum_and_plain_arithmetic():
+    """The oracle's rank-order merge of shard pairs, against its definition
+    written with the pinned TWO-SUM primitive and numpy's IEEE additions:
+    twofold variants (V, q) = TWO-SUM(V, V_g), E = (E + E_g) + q in binary64;
+    plain one addition in the data type; the binary32 output rule
+    v = RN32(V), e = RN32((V - v) + E); G = 0 and G = 1."""
+    rng = np.random.default_rng(70)
+    for G in (2, 3, 7):
+        pairs = np.stack([rng.standard_normal(G) * 10.0 ** rng.integers(-3, 3, size=G),
+                          rng.standard_normal(G) * 1e-17], axis=1)
+        V, E = pairs[0]
+        for g in range(1, G):
+            xs, ys = O.two_sum(np.array([V]), np.array([pairs[g, 0]]))
+            E = (E + pairs[g, 1]) + ys[0]
+            V = xs[0]
+        for variant in ("fast", "rigorous", "kahan", "fast_literal", "rigorous_literal"):
+            got = O.merge_pairs(pairs, np.float64, variant)
+            assert got[0] == V and got[1] == E, variant
+            got64 = O.merge_pairs(pairs, np.float32, variant, out_f64=True)
+            assert got64[0] == V and got64[1] == E
+            got32 = O.merge_pairs(pairs, np.float32, variant)
+            v = np.float32(V)
+            assert got32[0] == v and got32[1] == np.float32((V - np.float64(v)) + E)
+        p32 = pairs.astype(np.float32).astype(np.float64)
+        acc = np.float32(p32[0, 0])
+        for g in range(1, G):
+            acc = np.float32(acc + np.float32(p32[g, 0]))
+        got = O.merge_pairs(p32, np.float32, "plain")
+        assert got[0] == acc and got[1] == 0
+        acc64 = pairs[0, 0]
+        for g in range(1, G):
+            acc64 = acc64 + pairs[g, 0]
+        assert O.merge_pairs(pairs, np.float64, "plain")[0] == acc64
+    z = O.merge_pairs(np.zeros((0, 2)), np.float64, "rigorous")
+    assert z[0] == 0 and z[1] == 0 and not np.signbit(z[0])
+    one = O.merge_pairs(np.array([[3.0, 1e-20]]), np.float64, "fast")
+    assert one[0] == 3.0 and one[1] == 1e-20
+
+
+def test_merge_pairs_binary128_wide_exact_on_integers():
+    """binary64 'wide' pairs merge in binary128: on pairs whose exact sum fits
+    113 bits the result is (RN64(S), RN64(S - RN64(S))) of the exact S."""
+    from fractions import Fraction
+    rng = np.random.default_rng(71)
+    for G in (1, 2, 5):
+        hi = rng.integers(-2 ** 52, 2 ** 52, size=G).astype(np.float64) * 2.0 ** 40
+        lo = rng.integers(-2 ** 30, 2 ** 30, size=G).astype(np.float64)
+        S = sum(Fraction(float(a)) + Fraction(float(b)) for a, b in zip(hi, lo))
+        got = O.merge_pairs(np.stack([hi, lo], 1), np.float64, "wide")
+        assert Fraction(float(got[0])) + Fraction(float(got[1])) == S
+        assert got[0] == float(S)
+
+
+def test_split_reduction_obeys_the_bound():
+    """One ill-conditioned vector cut into G contiguous shards, each shard
+    replayed in the single-vector launch order (binary64 pair output), the
+    pairs merged in rank order: the merged pair meets the twofold bound with
+    the shard's depth plus G."""
+    import math
+    from _helpers import U64, twofold_bound, flat_depth
+    n = (1 << 18) + 3
+    ic = I.ill_conditioned(n, "f64", 1e14, seed=72)
+    x = ic.x.numpy()
+    for G in (2, 3, 8):
+        m = -(-n // (G * 2)) * 2
+        pairs = []
+        for g in range(G):
+            xs = x[min(g * m, n):min((g + 1) * m, n)]
+            pairs.append(O.replay_flat("sum", "rigorous", xs, block=128, unroll=2, grid=7))
+        got = O.merge_pairs(np.array(pairs), np.float64, "rigorous")
+        r = O.exact(x, v=float(got[0]), e=float(got[1]))
+        D = flat_depth(m, 2, 128, 2, 7) + G
+        assert abs(r.r) <= twofold_bound(r.s, r.sabs, U64, D)
+        assert abs(r.rv) > abs(r.r)
