@@ -33,10 +33,12 @@
  *   threads takes the 16-byte vectors j = g + P*m (m = 0, 1, ...) and feeds
  *   element l of vector j to its chain (m mod U)*V + l; a trailing partial
  *   vector is vector n/V.  Each thread folds its chains as a binary tree
- *   (c <- c + w for w = UV/2 ... 1), each warp by an xor butterfly (offsets
- *   16 ... 1), each block's warp pairs by the butterfly over block/32 lanes;
- *   the last block to finish folds the block pairs (thread t takes pairs
- *   t, t+block, ... in turn, then the same butterflies).
+ *   (c <- c + w for w = UV/2 ... 1).  Binary64 twofold variants fold each
+ *   block's thread pairs by the same tree (t <- t + w for w = block/2 ...
+ *   1); the others fold each warp by an xor butterfly (offsets 16 ... 1) and
+ *   the block's warp pairs by the butterfly over block/32 lanes.  The last
+ *   block to finish folds the block pairs (thread t takes pairs t, t+block,
+ *   ... in turn, then its thread pairs fold as a block's do).
  *   batched: the concatenated vector is cut into tiles of plan.tile elements;
  *   in a segment's piece of a tile, element at tile offset r goes to lane
  *   (r/V) mod 32, chain ((r/V)/32 mod U)*V + r mod V; lanes fold as above;

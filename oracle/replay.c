@@ -45,13 +45,16 @@
  *   floor(n/V) and is treated the same way.
  *   Each thread folds its U*V chains as a tree: for w = UV/2, ..., 1:
  *   chain[c] <- merge(chain[c], chain[c + w]) for c < w.
- *   Each warp of 32 threads folds as a butterfly: for o = 16, 8, 4, 2, 1:
- *   pair[i] <- merge(pair[i], pair[i xor o]); lane 0 holds the result.
- *   The W = B/32 warp pairs of a block fold by the same butterfly with
- *   o = W/2, ..., 1.
+ *   Binary64 twofold variants (fast, rigorous, kahan, the literal dots): the
+ *   B thread pairs of a block fold by the same tree: for w = B/2, ..., 1:
+ *   pair[t] <- merge(pair[t], pair[t + w]) for t < w; pair 0 is the block's.
+ *   The other variants: each warp of 32 threads folds as a butterfly: for
+ *   o = 16, 8, 4, 2, 1: pair[i] <- merge(pair[i], pair[i xor o]), lane 0
+ *   holding the result; the W = B/32 warp pairs of a block fold by the same
+ *   butterfly with o = W/2, ..., 1.
  *   Grid fold of the G block pairs: thread t of one block of B threads starts
  *   from pair t (identity if t >= G) and merges pairs t+B, t+2B, ... in turn;
- *   then the warp and block butterflies as above.  For binary32 data the
+ *   then the B thread pairs fold as a block's do.  For binary32 data the
  *   grid fold runs in binary64 (the block pairs widen exactly), except for
  *   the plain variant, which stays in binary32 throughout.
  *   Output for binary32 data from the binary64 pair (V, E):
@@ -234,6 +237,16 @@ static void write_out(const prob_t* P, pr_t r, int out_f64, void* out) {
 
 static int is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+/* the pair of a block's B thread pairs: the tree over the threads (binary64
+   twofold variants), else the butterfly of each warp and the butterfly over
+   the B/32 warp pairs */
+static pr_t block_pair(int f, int tw, int tree, pr_t* tp, int block) {
+    if (tree) return tree_fold(f, tw, tp, block);
+    pr_t wp[32];
+    for (int w = 0; w < block / 32; ++w) wp[w] = butterfly(f, tw, &tp[w * 32], 32);
+    return butterfly(f, tw, wp, block / 32);
+}
+
 int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y,
                     int64_t n, int block, int unroll, int64_t grid, int out_f64,
                     void* out) {
@@ -247,7 +260,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
     int64_t nv = n / V, tail = n - nv * V;
     int64_t Pth = grid * (int64_t)block;
     int fb = f_block(&P), fg = f_grid(&P), tw = twofold(&P);
-    int W = block / 32;
+    const int tree = (dtype == ORC_F64 && tw);       /* binary64 twofold: thread tree */
     pr_t* bp = (pr_t*)malloc(sizeof(pr_t) * (size_t)grid);
     pr_t* tp = (pr_t*)malloc(sizeof(pr_t) * (size_t)block);
     pr_t ch[64];
@@ -267,9 +280,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
             }
             tp[t] = tree_fold(fb, tw, ch, C);
         }
-        pr_t wp[32];
-        for (int w = 0; w < W; ++w) wp[w] = butterfly(fb, tw, &tp[w * 32], 32);
-        bp[b] = butterfly(fb, tw, wp, W);
+        bp[b] = block_pair(fb, tw, tree, tp, block);
     }
     /* grid fold: the block pairs widen exactly to the grid precision */
     pr_t res;
@@ -282,9 +293,7 @@ int orc_replay_flat(int dtype, int op, int variant, const void* x, const void* y
             }
             tp[t] = a;
         }
-        pr_t wp[32];
-        for (int w = 0; w < W; ++w) wp[w] = butterfly(fg, tw, &tp[w * 32], 32);
-        res = butterfly(fg, tw, wp, W);
+        res = block_pair(fg, tw, tree, tp, block);
     }
     write_out(&P, res, out_f64, out);
     free(bp); free(tp);

@@ -566,6 +566,12 @@ __device__ __forceinline__ q128 shfl_xor(q128 v, int o) {
     return q128(__shfl_xor_sync(FULL, v.lo, o), __shfl_xor_sync(FULL, v.hi, o));
 }
 
+template <typename A>
+__device__ __forceinline__ A shfl_down(A v, int o) { return __shfl_down_sync(FULL, v, o); }
+__device__ __forceinline__ q128 shfl_down(q128 v, int o) {
+    return q128(__shfl_down_sync(FULL, v.lo, o), __shfl_down_sync(FULL, v.hi, o));
+}
+
 // xor butterfly over the lanes of a warp for offsets o = W/2 ... 1; every
 // lane holds lane (lane ^ o)'s previous pair as second operand.
 template <bool TW, typename A>
@@ -594,6 +600,41 @@ __device__ __forceinline__ void block_fold(A& v, A& e, A* smem) {
         v = lane < W ? smem[lane] : A(0);
         e = lane < W ? smem[32 + lane] : A(0);
         warp_fold<TW>(v, e, W);
+    }
+    __syncthreads();
+}
+
+// Block fold as a tree over the block's threads: pair t <- merge(pair t,
+// pair t + w) for w = B/2, B/4, ..., 1 and threads t < w (the order of the
+// per-thread chain tree), through shared memory while w >= 32 and by
+// shuffles inside warp 0 below; each merge runs once, in one lane, so a fold
+// issues about a fifth of the binary64 instructions of a butterfly in which
+// every lane runs every merge.  Thread 0 returns the block pair; sv, se hold
+// blockDim.x values of A.  Ends with the block synchronized.
+template <bool TW, typename A>
+__device__ __forceinline__ void block_tree(A& v, A& e, A* sv, A* se) {
+    const int t = threadIdx.x, B = blockDim.x;
+    if (B > 32) {
+        sv[t] = v;
+        se[t] = e;
+        __syncthreads();
+        for (int w = B / 2; w >= 32; w >>= 1) {
+            if (t < w) {
+                A a = sv[t], ae = se[t];
+                merge<TW>(a, ae, sv[t + w], se[t + w]);
+                sv[t] = a;
+                se[t] = ae;
+            }
+            __syncthreads();
+        }
+        if (t < 32) { v = sv[t]; e = se[t]; }
+    }
+    if (t < 32) {
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1) {
+            const A v2 = shfl_down(v, w), e2 = shfl_down(e, w);
+            if (t < w) merge<TW>(v, e, v2, e2);
+        }
     }
     __syncthreads();
 }

@@ -4,10 +4,11 @@
 // 16-byte vectors j = g + P*m and feeds element l of vector j to its chain
 // (m mod U)*V + l, U vectors in flight per step.  The U*V chains hide the
 // dependency of each chain's additions (the latency chain the paper breaks
-// with independent accumulators in its h-functions).  Chains fold by a
-// tree, warps by an xor butterfly, blocks through shared memory; the last
-// block to finish (a ticket in the workspace, no waiting) folds the block
-// pairs in index order and writes the result.
+// with independent accumulators in its h-functions).  A thread's chains fold
+// by a tree; the block's threads by the same tree (binary64 twofold kernels)
+// or by warp butterflies and a butterfly over the warp pairs (the others);
+// the last block to finish (a ticket in the workspace, no waiting) folds the
+// block pairs the same way and writes the result.
 #include "tf_device.cuh"
 #include "tf_internal.h"
 
@@ -113,8 +114,14 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
         for (int c = 0; c < w; ++c) merge<TW>(s[c], e[c], s[c + w], e[c + w]);
     A v = s[0], ev = e[0];
 
+    // Binary64 twofold kernels fold blocks (and the grid) by the tree over the
+    // block's threads, where each merge's three binary64 adds run in one lane;
+    // the others keep the warp butterflies, whose merges are cheap there.
+    constexpr bool TREE = sizeof(T) == 8 && TW;
+    __shared__ __align__(16) double tree_buf[TREE ? 2 * 512 : 2];
     __shared__ A smA[64];
-    block_fold<TW>(v, ev, smA);
+    if constexpr (TREE) block_tree<TW>(v, ev, tree_buf, tree_buf + 512);
+    else block_fold<TW>(v, ev, smA);
 
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     G* slots = reinterpret_cast<G*>(ws + kWsHeader);
@@ -141,7 +148,8 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
         }
     }
     __shared__ G smG[64];
-    block_fold<TW>(gv, ge, smG);
+    if constexpr (TREE) block_tree<TW>(gv, ge, tree_buf, tree_buf + 512);
+    else block_fold<TW>(gv, ge, smG);
     if (threadIdx.x == 0) {
         write_out<T, VAR, G>(out, 0, gv, ge, out_f64 != 0);
         hdr->ticket = 0u;           // ready for the next call / graph replay

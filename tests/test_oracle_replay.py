@@ -76,6 +76,15 @@ def out_pair(dt, variant, r, out_f64):
     return np.array([v, np.float32(d)], dtype=np.float32)
 
 
+def block_pair(ar, tps, tree):
+    """a block's pair from its thread pairs: the tree over the threads, or the
+    butterfly of each warp and the butterfly over the warp pairs"""
+    if tree:
+        return ar.tree(tps)
+    wps = [ar.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(len(tps) // 32)]
+    return ar.butterfly(wps)
+
+
 def compose_flat(op, variant, x, y, block, unroll, grid, out_f64=False):
     dt = x.dtype.type
     f32 = dt == np.float32
@@ -86,6 +95,7 @@ def compose_flat(op, variant, x, y, block, unroll, grid, out_f64=False):
     tw = variant in TWOFOLD
     ab = Arith(f32 and variant != "wide", tw)
     ag = Arith(f32 and variant == "plain", tw)
+    tree = (not f32) and tw                    # binary64 twofold: the thread tree
     C = unroll * V
     bps = []
     for b in range(grid):
@@ -105,8 +115,7 @@ def compose_flat(op, variant, x, y, block, unroll, grid, out_f64=False):
                     lists[(m % unroll) * V + l].append(nv * V + l)
             ch = [chain_pair(op, variant, x, y, np.array(li, dtype=np.int64)) for li in lists]
             tps.append(ab.tree(ch))
-        wps = [ab.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
-        bps.append(ab.butterfly(wps))
+        bps.append(block_pair(ab, tps, tree))
     tps = []
     for t in range(block):
         a = (0.0, 0.0)
@@ -115,8 +124,7 @@ def compose_flat(op, variant, x, y, block, unroll, grid, out_f64=False):
             for i in range(t + block, grid, block):
                 a = ag.merge(a, bps[i])
         tps.append(a)
-    wps = [ag.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
-    return out_pair(dt, variant, ag.butterfly(wps), out_f64)
+    return out_pair(dt, variant, block_pair(ag, tps, tree), out_f64)
 
 
 CASES = [
@@ -198,6 +206,7 @@ def compose_csr(op, variant, x, y, off, unroll, tile, out_f64=False):
     tw = variant in TWOFOLD
     ab = Arith(f32 and variant != "wide", tw)
     ag = Arith(f32 and variant == "plain", tw)
+    tree = (not f32) and tw                    # binary64 twofold: the thread tree
     C = unroll * V
     outs = []
     for s in range(off.size - 1):
@@ -369,8 +378,7 @@ def compose_flat_q(x, y, block, unroll, grid):
             if tail and g == nv % P:
                 lists[((nv // P) % unroll) * V].append(nv * V)
             tps.append(q.tree([chain_q(x, y, li) for li in lists]))
-        wps = [q.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
-        bps.append(q.butterfly(wps))
+        bps.append(block_pair(q, tps, False))
     tps = []
     for t in range(block):
         a = Fraction(0)
@@ -379,8 +387,7 @@ def compose_flat_q(x, y, block, unroll, grid):
             for i in range(t + block, grid, block):
                 a = q.merge(a, bps[i])
         tps.append(a)
-    wps = [q.butterfly(tps[w * 32:(w + 1) * 32]) for w in range(block // 32)]
-    return out_q(q.butterfly(wps))
+    return out_q(block_pair(q, tps, False))
 
 
 @pytest.mark.parametrize("op,n,block,unroll,grid", [
