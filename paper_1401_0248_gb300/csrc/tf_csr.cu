@@ -81,10 +81,12 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
     constexpr int V = 16 / sizeof(T);
     constexpr int C = U * V;
     constexpr int SV = 32 * V;              // elements per warp-wide slot row
-    // binary32 data streams at the memory's pace: load the next full step
-    // while the current one is fed (the binary64 and wide kernels are bound
-    // by their arithmetic and keep the registers instead)
-    constexpr bool PREFETCH = sizeof(T) == 4 && VAR != WIDE;
+    // load the next full step while the current one is fed: binary32 data
+    // (it streams at the memory's pace) and the binary64 twofold sums (their
+    // arithmetic outlasts a load only with many warps per SM); the binary64
+    // dots and the wide kernels keep the registers instead (measured)
+    constexpr bool PREFETCH = (sizeof(T) == 4 && VAR != WIDE) ||
+                              (sizeof(T) == 8 && !DOT && (VAR == FAST || VAR == RIGOROUS));
 
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
