@@ -685,6 +685,38 @@ def run_c5(args, dev, stream, hbm):
     return res
 
 
+def run_misaligned(args, data, dev, stream):
+    """The cost of an input that is element-aligned but not 16-byte aligned:
+    the kernels then load it with scalar loads in the same order (same bits).
+    The step's binary32 fast sum and binary64 fast dot (cond 1e8), timed on
+    views that start one element into the arrays, against the aligned views
+    of the same n - 1 elements."""
+    import torch
+    from paper_1401_0248_gb300 import twofold as tf
+    cond = 1e8 if 1e8 in args.conds else args.conds[0]
+    res = {"config": "views one element into the step's arrays (n - 1 elements)", "kernels": {}}
+    reps = max(5, min(args.steps, 10))
+    for dt, op in (("f32", "sum"), ("f64", "dot")):
+        x, y, _, _ = data[(dt, cond)][op]
+        n = x.numel() - 1
+        xa, xm = x[:n].clone(), x[1:]
+        ya, ym = (y[:n].clone(), y[1:]) if y is not None else (None, None)
+        ws = torch.zeros(tf.workspace_size(op, False, x.dtype, "fast", n), dtype=torch.uint8,
+                         device=dev)
+        out = torch.empty(2, dtype=x.dtype, device=dev)
+        ms = {}
+        for name, xx, yy in (("aligned", xa, ya), ("misaligned", xm, ym)):
+            call = ((lambda xx=xx: tf.sum(xx, "fast", out=out, ws=ws)) if op == "sum" else
+                    (lambda xx=xx, yy=yy: tf.dot(xx, yy, "fast", out=out, ws=ws)))
+            ms[name] = _time_calls(call, stream, args.warmup, reps)
+        res["kernels"]["%s_%s_fast" % (dt, op)] = {
+            "aligned_ms": round(ms["aligned"], 4), "misaligned_ms": round(ms["misaligned"], 4),
+            "slowdown": round(ms["misaligned"] / ms["aligned"], 3)}
+        del xa, ya
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_small(dev, stream, reps=20):
     """The L2-resident case: N = 2^20 binary64 (8 MiB per operand), uniform
     [-1, 1).  Launches are replayed from CUDA graphs so that the host's call
@@ -1145,6 +1177,9 @@ def main(argv=None):
                                      torch.cuda.current_stream(torch.device("cuda", local)))
         res["small"] = run_small(torch.device("cuda", local),
                                  torch.cuda.current_stream(torch.device("cuda", local)))
+    if not args.no_batched:
+        d = torch.device("cuda", local)
+        res["misaligned"] = run_misaligned(args, data, d, torch.cuda.current_stream(d))
     if not args.no_large:
         d = torch.device("cuda", local)
         hbm, _ = load_peaks()
