@@ -50,12 +50,12 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
             for (int l = 0; l < V; ++l)
                 feed<VAR, DOT>(s[u * V + l], e[u * V + l], xv[u][l], DOT ? yv[u][l] : T(0), one);
     };
-    // binary32 twofold dots and binary64 twofold sums: the next step's loads
-    // go out before this step's arithmetic (two steps of loads in flight per
-    // thread).  Binary64 dots do not: the extra registers cost them more
-    // occupancy than the overlap gains (measured).
+    // binary32 twofold dots and binary64 twofold sums and dots: the next
+    // step's loads go out before this step's arithmetic (two steps of loads
+    // in flight per thread; the binary64 plans keep one 16-byte load per
+    // array per step, U = 1, so the extra registers leave occupancy intact)
     constexpr bool PREFETCH = (sizeof(T) == 4 && DOT && VAR != WIDE) ||
-                              (sizeof(T) == 8 && !DOT && (VAR == FAST || VAR == RIGOROUS));
+                              (sizeof(T) == 8 && (VAR == FAST || VAR == RIGOROUS));
     if constexpr (PREFETCH) {
         if (j + (U - 1) * P < nv) {
             T xv[U][V], yv[U][V];
