@@ -850,8 +850,19 @@ def _batched_kernels(args, tf, dev, stream, res, dt, td, variants, x, y, off, n,
             ms = a.elapsed_time(b) / reps
             byts = nbytes(dt, op, n) + 8 * (nseg + 1) + 2 * (4 if dt == "f32" else 8) * nseg
             gbs = byts / (ms * 1e-3) / 1e9
-            res["kernels"]["%s_%s_%s" % (dt, op, v)] = {"ms": round(ms, 4), "gbs": round(gbs, 1),
-                                                        "frac_hbm": round(gbs / hbm, 4)}
+            ent = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 4)}
+            if v != "plain":
+                # the single-vector kernel on the same concatenated data: what
+                # the segments cost beside one long reduction
+                fws = torch.zeros(tf.workspace_size(op, False, td, v, n), dtype=torch.uint8,
+                                  device=dev)
+                fo = torch.empty(2, dtype=td, device=dev)
+                fcall = ((lambda v=v: tf.sum(x, v, ws=fws, out=fo)) if op == "sum" else
+                         (lambda v=v: tf.dot(x, y, v, ws=fws, out=fo)))
+                fms = _time_calls(fcall, stream, args.warmup, max(5, min(args.steps, 10)))
+                ent["flat_same_data_ms"] = round(fms, 4)
+                ent["batched_over_flat"] = round(ms / fms, 4)
+            res["kernels"]["%s_%s_%s" % (dt, op, v)] = ent
             del g
 
 
