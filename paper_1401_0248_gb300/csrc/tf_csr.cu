@@ -77,7 +77,6 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
            int out_f64) {
     using A = typename Acc<T, VAR>::type;
     using G = typename GridAcc<T, VAR>::type;
-    constexpr bool TW = twofold_v<VAR>;
     constexpr int V = 16 / sizeof(T);
     constexpr int C = U * V;
     constexpr int SV = 32 * V;              // elements per warp-wide slot row

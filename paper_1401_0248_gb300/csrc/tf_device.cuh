@@ -450,6 +450,12 @@ template <> struct GridAcc<double, WIDE> { using type = q128; };
 
 __device__ __forceinline__ q128 add_rn(q128 a, q128 b) { return q_add(a, b); }
 
+// Shared-memory storage of a value type: the type itself, or for q128 (whose
+// constructor a __shared__ variable may not run) a plain struct of its layout.
+template <typename A> struct SmemOf { using type = A; };
+struct q128_raw { unsigned long long lo, hi; };
+template <> struct SmemOf<q128> { using type = q128_raw; };
+
 template <int VAR> constexpr bool twofold_v = (VAR != PLAIN && VAR != WIDE);
 // the per-item step after the product: literal dots step like the sums
 template <int VAR> constexpr int step_v = VAR == FAST_LIT ? FAST : (VAR == RIG_LIT ? RIGOROUS : VAR);

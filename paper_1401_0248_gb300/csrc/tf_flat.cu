@@ -119,9 +119,9 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
     // the others keep the warp butterflies, whose merges are cheap there.
     constexpr bool TREE = sizeof(T) == 8 && TW;
     __shared__ __align__(16) double tree_buf[TREE ? 2 * 512 : 2];
-    __shared__ A smA[64];
+    __shared__ typename SmemOf<A>::type smA[64];
     if constexpr (TREE) block_tree<TW>(v, ev, tree_buf, tree_buf + 512);
-    else block_fold<TW>(v, ev, smA);
+    else block_fold<TW>(v, ev, reinterpret_cast<A*>(smA));
 
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     G* slots = reinterpret_cast<G*>(ws + kWsHeader);
@@ -147,9 +147,9 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
             merge<TW>(gv, ge, v2, e2);
         }
     }
-    __shared__ G smG[64];
+    __shared__ typename SmemOf<G>::type smG[64];
     if constexpr (TREE) block_tree<TW>(gv, ge, tree_buf, tree_buf + 512);
-    else block_fold<TW>(gv, ge, smG);
+    else block_fold<TW>(gv, ge, reinterpret_cast<G*>(smG));
     if (threadIdx.x == 0) {
         write_out<T, VAR, G>(out, 0, gv, ge, out_f64 != 0);
         hdr->ticket = 0u;           // ready for the next call / graph replay
