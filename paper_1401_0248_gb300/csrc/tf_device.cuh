@@ -251,22 +251,22 @@ __device__ __forceinline__ bool two_product_i64(double a, double b, double& p, d
     const unsigned int m = 2u - top;
     hi = hi * m + ((lo >> 63) & (unsigned long long)(1u - top));
     lo = lo * m;                                           // now in [2^105, 2^106)
-    unsigned long long q = (hi << 11) | (lo >> 53);
+    const unsigned long long q = (hi << 11) | (lo >> 53);     // [2^52, 2^53)
     const unsigned long long rem = lo & ((1ull << 53) - 1ull);
-    const unsigned long long half = 1ull << 52;
-    const bool up = rem > half || (rem == half && (q & 1ull));
-    const unsigned long long rmag = up ? ((1ull << 53) - rem) : rem;
-    q += up ? 1ull : 0ull;
-    int ex = es - 1023 + (int)top;
-    if (q == (1ull << 53)) { q >>= 1; ex += 1; }
+    // round to nearest even by a carry: q rounds up exactly when
+    // rem + 2^52 - 1 + (q & 1) reaches 2^53; then ab - p = rem - 2^53
+    const unsigned long long c = (rem + ((1ull << 52) - 1ull) + (q & 1ull)) >> 53;
     const unsigned long long sg = (A ^ B) >> 63;
-    p = __longlong_as_double((long long)((sg << 63) | ((unsigned long long)ex << 52) | (q & M52)));
+    // exponent field es - 1023 + top; q + c = 2^53 carries into it
+    p = __longlong_as_double((long long)((sg << 63) |
+                                         (((unsigned long long)(es - 1024 + (int)top) << 52) + q + c)));
+    const unsigned long long rmag = c ? ((1ull << 53) - rem) : rem;
     if (rmag == 0ull) {
         e = 0.0;
     } else {
         // rmag counts units of 2^(es - 2151 + top)
         const int pr = 63 - __clzll((long long)rmag);          // <= 52
-        const unsigned long long se = sg ^ (up ? 1ull : 0ull);
+        const unsigned long long se = sg ^ c;
         e = __longlong_as_double((long long)((se << 63) |
                                              ((unsigned long long)(es + pr - 1128 + (int)top) << 52) |
                                              ((rmag << (52 - pr)) & M52)));
