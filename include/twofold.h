@@ -41,7 +41,9 @@
  *   ... in turn, then its thread pairs fold as a block's do).
  *   batched: the concatenated vector is cut into tiles of plan.tile elements;
  *   in a segment's piece of a tile, element at tile offset r goes to lane
- *   (r/V) mod 32, chain ((r/V)/32 mod U)*V + r mod V; lanes fold as above;
+ *   (r/V) mod 32, chain ((r/V)/32 mod U)*V + r mod V; each lane folds its
+ *   chains as above and the warp's lanes fold by the xor butterfly (offsets
+ *   16 ... 1) for every variant;
  *   a segment spanning k <= 32 tiles merges its k piece pairs as 32 lanes
  *   (lane l holds piece l, +0 pairs after k) and the butterfly; beyond 32 by
  *   a pairwise tree in tile order (the pair of piece j, j a multiple of 2w,
@@ -138,8 +140,9 @@ tf_status tf_dot(const void* x, const void* y, int64_t n, tf_dtype dtype,
    offsets[s+1]).  x holds n elements; offsets (device, int64, nseg + 1
    entries) must satisfy offsets[0] = 0, offsets[s] <= offsets[s+1],
    offsets[nseg] <= n.  out receives nseg pairs (2*nseg elements, or doubles
-   with TF_OUT_F64).  Enqueues two kernels: an offsets check and one
-   persistent reduction over all segments.  Invalid offsets are detected on
+   with TF_OUT_F64).  Enqueues three kernels: an offsets check, one
+   persistent reduction over all segments, and the merge of the pieces of the
+   segments over 2..32 tiles.  Invalid offsets are detected on
    the device: every output pair is set to NaN and the workspace error word
    to TF_ERR_OFFSETS (read it with tf_get_device_error). */
 tf_status tf_sum_batched(const void* x, int64_t n, const int64_t* offsets, int64_t nseg,

@@ -10,18 +10,22 @@
 // tile, slot m feeding chains (m mod U)*V + (element mod V).  Elements
 // outside the piece are fed as +0, which leaves a twofold, plain or wide
 // chain's bits unchanged (Kahan chains skip them), so the chain assignment is
-// the documented one.  A segment inside one tile is written directly; the k
-// pieces of a segment over k tiles merge by a pairwise tree in tile order,
-// each merge done by the warp that completes the second of its two children
-// (arrival counters, no waiting), so which warp reduces which tile never
-// changes a bit.  A first small kernel checks the offsets, clears the
-// counters, writes the empty segments and records the segment holding each
-// tile's first element.
+// the documented one.  A segment inside one tile is written directly.  The
+// pieces of a segment over 2..32 tiles are stored, and a merge kernel
+// launched after the reduction merges them (one thread per segment, the
+// kernel boundary ordering the stores before the loads: no atomics on the
+// streaming warps); over more than 32 tiles they merge by a pairwise tree in
+// tile order, each merge done by the warp that completes the second of its
+// two children (arrival counters, no waiting).  Which warp reduces which
+// tile never changes a bit.  A first small kernel checks the offsets, clears
+// the counters, writes the empty segments and records the segment holding
+// each tile's first element.
 #include "tf_csr.cuh"
 
 namespace tf {
 
 constexpr int kTfErrOffsets = 6;       // TF_ERR_OFFSETS
+constexpr int kMergeThreads = 256;     // csr_merge: one thread per tile
 
 size_t csr_ws_bytes(int64_t n, int64_t nseg) {
     (void)nseg;
@@ -34,6 +38,7 @@ __global__ void csr_prepare(const int64_t* __restrict__ off, int64_t nseg, int64
                             int64_t tile, void* __restrict__ out, unsigned char* __restrict__ ws,
                             int64_t* __restrict__ tile_seg, int out_f64) {
     using G = typename GridAcc<T, VAR>::type;
+    grid_dependents_go();
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -87,12 +92,14 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
     constexpr bool PREFETCH = (sizeof(T) == 4 && VAR != WIDE) ||
                               (sizeof(T) == 8 && !DOT && (VAR == FAST || VAR == RIGOROUS));
 
+    grid_wait();                      // the offsets check has completed
+    grid_dependents_go();
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     G* pieces = reinterpret_cast<G*>(ws + kWsHeader + cnt_bytes);
     const int lane = threadIdx.x & 31;
-    double one = 1.0;                 // binary64 sums, wide: a 1.0 the compiler cannot see
-    if constexpr ((sizeof(T) == 8 && !DOT) || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
+    double one = 1.0;                 // binary64 data, wide: a 1.0 the compiler cannot see
+    if constexpr (sizeof(T) == 8 || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const bool bad = *reinterpret_cast<volatile int*>(&hdr->call_bad) != 0;
     if (bad) {
@@ -114,6 +121,7 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
             const int64_t thi = min(tlo + tile, total);
             int64_t s = __ldg(tile_seg + t);
             int64_t a = __ldg(off + s), b = __ldg(off + s + 1);
+            int64_t bn = __ldg(off + min(s + 2, nseg));   // the next segment's end, loaded ahead
             for (;;) {
                 const int64_t pa = max(a, tlo), pb = min(b, thi);
                 if (pb > pa) {
@@ -217,27 +225,48 @@ csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __re
                 if (b > thi) break;                 // segment continues in the next tile
                 if (++s >= nseg) break;
                 a = b;
-                b = __ldg(off + s + 1);
+                b = bn;
+                bn = __ldg(off + min(s + 2, nseg));
                 if (a >= thi) break;                // next segment starts in a later tile
             }
             t = __shfl_sync(FULL, tn, 0);
         }
     }
+}
 
-    // the last block to finish clears the per-call flag and the tile counter
-    __syncthreads();
-    __shared__ int am_last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned int tk = atomicAdd(&hdr->ticket2, 1u);
-        am_last = (tk == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (am_last && threadIdx.x == 0) {
+// The segments over 2..32 tiles, after the reduction kernel has stored their
+// piece pairs: thread t reads k from the word of slot 2t + 1 (0 unless a
+// segment over k >= 2 tiles starts in tile t; the offsets check cleared it)
+// and merges that segment's k pieces in the butterfly order
+// (butterfly_node); the segment is the one holding tile t + 1's first
+// element.  The reduction kernel has finished, so thread 0 clears the
+// per-call flag and the tile counter.
+template <typename T, int VAR>
+__global__ void __launch_bounds__(kMergeThreads)
+csr_merge(void* __restrict__ out, unsigned char* __restrict__ ws, size_t cnt_bytes,
+          const int64_t* __restrict__ tile_seg, int64_t ntiles, int out_f64) {
+    using G = typename GridAcc<T, VAR>::type;
+    constexpr bool TW = twofold_v<VAR>;
+    grid_wait();                      // the reduction has completed
+    const unsigned int* cnt = reinterpret_cast<const unsigned int*>(ws + kWsHeader);
+    const G* pieces = reinterpret_cast<const G*>(ws + kWsHeader + cnt_bytes);
+    const int64_t t = (int64_t)blockIdx.x * kMergeThreads + threadIdx.x;
+    if (t == 0) {
+        WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
         hdr->call_bad = 0;
         hdr->tile_next = 0ull;
-        hdr->ticket2 = 0u;
     }
+    if (t + 1 >= ntiles) return;
+    const int k = (int)cnt[2 * t + 1];
+    if (k < 2) return;
+    const int64_t s = __ldg(tile_seg + t + 1);
+    G v, e;
+    if (k <= 2) butterfly_node<1, 2, TW>(pieces, t, k, 0, v, e);
+    else if (k <= 4) butterfly_node<1, 4, TW>(pieces, t, k, 0, v, e);
+    else if (k <= 8) butterfly_node<1, 8, TW>(pieces, t, k, 0, v, e);
+    else if (k <= 16) butterfly_node<1, 16, TW>(pieces, t, k, 0, v, e);
+    else butterfly_node<1, 32, TW>(pieces, t, k, 0, v, e);
+    write_out<T, VAR, G>(out, s, v, e, out_f64 != 0);
 }
 
 template <typename T, int VAR, bool DOT>
@@ -254,19 +283,28 @@ static cudaError_t launch_u(int unroll, const void* x, const void* y, int64_t n,
     const int pblocks = (int)std::min<int64_t>(1024, (items + 255) / 256);
     csr_prepare<T, VAR><<<pblocks, 256, 0, st>>>(off, nseg, n, tile, out, w, tile_seg, out_f64);
     cudaError_t err = cudaGetLastError();
+    const int64_t* ctile_seg = tile_seg;
     if (err != cudaSuccess) return err;
-    if (aligned && staged && csr_tma_usable(sizeof(T) == 4 ? 0 : 1, DOT ? 1 : 0, block, tile))
-        return launch_csr_tma(sizeof(T) == 4 ? 0 : 1, VAR, DOT ? 1 : 0, unroll, x, y, off, nseg, out,
-                              w, cnt_bytes, tile_seg, block, grid, tile, out_f64, st);
-    const T* xp = static_cast<const T*>(x);
-    const T* yp = static_cast<const T*>(y);
-    switch (unroll) {
-    case 1: csr_kernel<T, VAR, DOT, 1><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile_seg, tile, aligned, out_f64); break;
-    case 2: csr_kernel<T, VAR, DOT, 2><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile_seg, tile, aligned, out_f64); break;
-    case 4: csr_kernel<T, VAR, DOT, 4><<<(unsigned)grid, block, 0, st>>>(xp, yp, off, nseg, out, w, cnt_bytes, tile_seg, tile, aligned, out_f64); break;
-    default: return cudaErrorInvalidValue;
+    if (aligned && staged && csr_tma_usable(sizeof(T) == 4 ? 0 : 1, DOT ? 1 : 0, block, tile)) {
+        err = launch_csr_tma(sizeof(T) == 4 ? 0 : 1, VAR, DOT ? 1 : 0, unroll, x, y, off, nseg, out,
+                             w, cnt_bytes, tile_seg, block, grid, tile, out_f64, st);
+    } else {
+        const T* xp = static_cast<const T*>(x);
+        const T* yp = static_cast<const T*>(y);
+        switch (unroll) {
+        case 1: err = launch_dependent(csr_kernel<T, VAR, DOT, 1>, (unsigned)grid, (unsigned)block, 0, st, xp, yp, off, nseg, out, w, cnt_bytes, ctile_seg, tile, aligned, out_f64); break;
+        case 2: err = launch_dependent(csr_kernel<T, VAR, DOT, 2>, (unsigned)grid, (unsigned)block, 0, st, xp, yp, off, nseg, out, w, cnt_bytes, ctile_seg, tile, aligned, out_f64); break;
+        case 4: err = launch_dependent(csr_kernel<T, VAR, DOT, 4>, (unsigned)grid, (unsigned)block, 0, st, xp, yp, off, nseg, out, w, cnt_bytes, ctile_seg, tile, aligned, out_f64); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
-    return cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    // one thread per tile of n elements (they cover those of offsets[nseg] <= n;
+    // the words of tiles past offsets[nseg] stay 0)
+    const int64_t ntiles = (n + tile - 1) / tile;
+    const int64_t mblocks = std::max<int64_t>(1, (ntiles + kMergeThreads - 1) / kMergeThreads);
+    return launch_dependent(csr_merge<T, VAR>, (unsigned)mblocks, (unsigned)kMergeThreads, 0, st,
+                            out, w, cnt_bytes, ctile_seg, ntiles, out_f64);
 }
 
 template <typename T, int VAR>

@@ -59,12 +59,14 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
     extern __shared__ __align__(128) unsigned char ring_all[];
     __shared__ __align__(8) unsigned long long bars[kMaxWarps * kStages];
 
+    grid_wait();                      // the offsets check has completed
+    grid_dependents_go();
     WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(ws + kWsHeader);
     G* pieces = reinterpret_cast<G*>(ws + kWsHeader + cnt_bytes);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double one = 1.0;                 // binary64 sums, wide: a 1.0 the compiler cannot see
-    if constexpr ((sizeof(T) == 8 && !DOT) || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
+    double one = 1.0;                 // binary64 data, wide: a 1.0 the compiler cannot see
+    if constexpr (sizeof(T) == 8 || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const uint32_t ring = smem_u32(ring_all) + (uint32_t)(wib * kStages * kStageBytes);
     const uint32_t bar0 = smem_u32(&bars[wib * kStages]);
@@ -137,6 +139,7 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
             top_up();
             int64_t s = __ldg(tile_seg + t);
             int64_t a = __ldg(off + s), b = __ldg(off + s + 1);
+            int64_t bn = __ldg(off + min(s + 2, nseg));   // the next segment's end, loaded ahead
             int cur = -1;                          // chunk of the tile being read
 
             // chunks before ch are read: free them, refill the ring, wait for ch
@@ -245,7 +248,8 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
                 if (b > thi) break;                 // segment continues in the next tile
                 if (++s >= nseg) break;
                 a = b;
-                b = __ldg(off + s + 1);
+                b = bn;
+                bn = __ldg(off + min(s + 2, nseg));
                 if (a >= thi) break;                // next segment starts in a later tile
             }
             if (failed) break;
@@ -275,21 +279,6 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
                 drained = mbar_wait(bar0 + 8 * (k % kStages), (k / kStages) & 1u, kWaitLimit) && drained;
             if (!drained && lane == 0) atomicExch(&hdr->error, kTfErrUndrained);
         }
-    }
-
-    // the last block to finish clears the per-call flag and the tile counter
-    __syncthreads();
-    __shared__ int am_last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned int tk = atomicAdd(&hdr->ticket2, 1u);
-        am_last = (tk == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (am_last && threadIdx.x == 0) {
-        hdr->call_bad = 0;
-        hdr->tile_next = 0ull;
-        hdr->ticket2 = 0u;
     }
 }
 
@@ -326,8 +315,8 @@ static cudaError_t launch_tma_u(const T* x, const T* y, const int64_t* off, int6
         if (e != cudaSuccess) return e;
         raised.fetch_or(bit);
     }
-    kern<<<(unsigned)grid, block, smem, st>>>(x, y, off, nseg, out, ws, cnt_bytes, tile_seg, tile, out_f64);
-    return cudaGetLastError();
+    return launch_dependent(kern, (unsigned)grid, (unsigned)block, smem, st, x, y, off, nseg, out,
+                            ws, cnt_bytes, tile_seg, tile, out_f64);
 }
 
 template <typename T, int VAR, bool DOT>

@@ -133,8 +133,9 @@ __device__ __forceinline__ double sum_error_h64(unsigned long long A, unsigned l
 // A binary64 add issued as a fused multiply-add by `one` == 1.0: RN(a*1 + b)
 // = RN(a + b) for every input, signed zeros included (-0*1 + +0 = +0,
 // -0*1 + -0 = -0).  GB300 issues DFMA at 626 G/s against DADD's 528 G/s, so
-// the binary64 sums add this way; `one` must be a value the compiler cannot
-// see (a load of g_one), since a known 1.0 is folded back into a DADD.
+// the per-item steps on binary64 add this way (the merges keep DADD); `one`
+// must be a value the compiler cannot see (a load of g_one), since a known
+// 1.0 is folded back into a DADD.
 static __device__ double g_one = 1.0;   // never written: read once per kernel as `one`
 
 template <bool FMA>
@@ -470,13 +471,14 @@ template <int VAR> constexpr int step_v = VAR == FAST_LIT ? FAST : (VAR == RIG_L
 //   plain:                s = s + y
 //   wide:                 S = S + y in binary64 (binary32 products are exact
 //                         in binary64)
-// `one` is a runtime 1.0 (see dadd): binary64 sums and the binary64
-// accumulator of binary32 data ('wide') issue their adds as DFMA.
+// `one` is a runtime 1.0 (see dadd): the binary64 sums and twofold dots and
+// the binary64 accumulator of binary32 data ('wide') issue their adds as DFMA
+// (the plain binary64 dot rounds its product first, by a multiply).
 template <int VAR, bool DOT, typename T, typename A>
 __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
     constexpr int STEP = step_v<VAR>;
     constexpr bool TPROD = DOT && (VAR == FAST || VAR == RIGOROUS);   // TwoProduct error kept
-    constexpr bool FMA = sizeof(T) == 8 && !DOT;
+    constexpr bool FMA = sizeof(T) == 8 && (!DOT || VAR != PLAIN);
     if constexpr (VAR == WIDE && sizeof(T) == 8) {
         // binary64 data: binary128 accumulator, products exact in binary128
         s = q_add(s, DOT ? q_mul_exact(a, b) : q128(a));
@@ -521,7 +523,7 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
             } else {
                 if (!two_sum_h64<FMA>(s, p, t, y, one)) { const double2 r = two_sum_slow(s, p); t = r.x; y = r.y; }
             }
-            if constexpr (TPROD) e = add_rn(e, add_rn(y, ep)); else e = dadd<FMA>(e, y, one);
+            if constexpr (TPROD) e = dadd<FMA>(e, dadd<FMA>(y, ep, one), one); else e = dadd<FMA>(e, y, one);
         }
         s = t;
     } else {
@@ -683,10 +685,10 @@ __device__ __forceinline__ void ld_pair_cg(const q128* p, q128& v, q128& e) {
 struct WsHeader {
     unsigned int ticket;     // single vector: blocks done (reset by the last)
     int error;               // device error word, sticky until the host reads it
-    int call_bad;            // batched: offsets of the current call are invalid
-    unsigned int ticket2;    // batched: blocks done (reset by the last)
+    int call_bad;            // batched: offsets of the current call are invalid (cleared by csr_merge)
+    unsigned int reserved;
     double stage[2];         // host-buffer calls: the output pair
-    unsigned long long tile_next;   // batched: next tile to claim (reset by the last block)
+    unsigned long long tile_next;   // batched: next tile to claim (cleared by csr_merge)
 };
 constexpr size_t kWsHeader = 256;
 

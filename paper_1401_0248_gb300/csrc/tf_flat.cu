@@ -27,8 +27,8 @@ flat_kernel(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
     A s[C], e[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) { s[c] = A(0); e[c] = A(0); }
-    double one = 1.0;                 // binary64 sums, wide: a 1.0 the compiler cannot see
-    if constexpr ((sizeof(T) == 8 && !DOT) || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
+    double one = 1.0;                 // binary64 data, wide: a 1.0 the compiler cannot see
+    if constexpr (sizeof(T) == 8 || VAR == WIDE) one = *reinterpret_cast<volatile double*>(&g_one);
 
     const int64_t nv = n / V;
     const int tail = (int)(n - nv * V);

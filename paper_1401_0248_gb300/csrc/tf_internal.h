@@ -18,9 +18,9 @@ cudaError_t launch_flat(int dtype, int variant, int dot, int unroll, const void*
                         const void* y, int64_t n, void* out, void* ws, int block,
                         int64_t grid, int aligned, int out_f64, cudaStream_t st);
 
-// batched reduction: the offsets check, then the persistent kernel (the
+// batched reduction: the offsets check, the persistent kernel (the
 // shared-memory ring one when `staged` and the plan fits its ring, else the
-// register-loading one)
+// register-loading one), then the merge of the segments over 2..32 tiles
 cudaError_t launch_csr(int dtype, int variant, int dot, int unroll, const void* x,
                        const void* y, int64_t n, const int64_t* off, int64_t nseg,
                        void* out, void* ws, size_t ws_bytes, int block, int64_t grid,

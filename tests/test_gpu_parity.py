@@ -510,6 +510,29 @@ def test_csr_tiles_and_long_segments(tile, bps):
 
 
 @pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_csr_segment_over_thousands_of_tiles(dt):
+    """A segment over 2,501 tiles of 1024 (its pairwise tree of pieces runs
+    twelve levels), between segments of 1 to 33 tiles and segments ending on
+    tile edges; the variants whose cross-tile pair types differ (binary64,
+    the binary128 accumulator), plain and the Kahan chains."""
+    tile = 1024
+    L = [5, tile - 5, tile * 2500 + 7, tile * 33 - 7, 1, tile * 32, 3, tile + 1]
+    off_h = I.csr_offsets(L)
+    n = int(off_h[-1])
+    x = I.normal(n, dt, seed=21, device=DEV)
+    y = I.normal(n, dt, seed=21, stream=4, device=DEV)
+    for op, variant in (("sum", "rigorous"), ("dot", "fast"), ("sum", "wide"), ("sum", "kahan"),
+                        ("sum", "plain")):
+        before = tf.plan_get(op, True, TD[dt], variant)
+        try:
+            tf.plan_set(op, True, TD[dt], variant, 256, 1, 2, tile)
+            check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
+        finally:
+            tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
+                        before["blocks_per_sm"], before["tile"])
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
 @pytest.mark.parametrize("unroll,block", [(1, 128), (2, 512), (4, 256)])
 def test_csr_staged_ring_edges(dt, unroll, block):
     """The shared-memory ring of the batched kernel (16-byte-aligned inputs,
