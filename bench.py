@@ -72,9 +72,10 @@ NOMINAL_HBM_GBS = 7900.0
 # Binary64-pipe instructions per element that the binary64 kernels issue:
 # the twofold steps keep two roundings on the binary64 pipe (t = s + p and
 # e = e + y; dots also q + ep) and compute the exact error terms and the
-# product on the integer pipe; plain keeps its add (and multiply).  The sums
-# issue their adds as DFMA by 1.0 (the faster binary64 instruction on GB300),
-# the dots as DADD; each is held against its own measured rate.
+# product on the integer pipe; plain keeps its add (and multiply).  The
+# twofold kernels and the plain sum issue their adds as DFMA by 1.0 (the
+# faster binary64 instruction on GB300), the plain dot as DADD after its
+# multiply; each is held against its own measured rate.
 FP64_PIPE_OPS = {("sum", "plain"): 1, ("sum", "fast"): 2, ("sum", "rigorous"): 2,
                  ("dot", "plain"): 2, ("dot", "fast"): 3, ("dot", "rigorous"): 3}
 # the paper's operation counts (Examples 1 and 3; dots add TwoProduct and one add)
@@ -422,9 +423,9 @@ def run_gpu(args, rank, world, local):
     if dt == "f64":
         # what limits the binary64 kernels: the binary64 pipe (with the exact
         # error terms on the integer pipe); its issued adds against the
-        # measured rate of the instruction they use (DFMA by 1.0 for sums,
-        # DADD for dots)
-        fma_adds = op == "sum"
+        # measured rate of the instruction they use (DFMA by 1.0, except the
+        # plain dot's DADD)
+        fma_adds = op == "sum" or v != "plain"
         peak_ops = (probes or {}).get("dadd_as_fma_gops" if fma_adds else "dadd_gops") \
             or (FALLBACK_DFMA_GOPS if fma_adds else FALLBACK_DADD_GOPS)
         ops = FP64_PIPE_OPS[(op, v)] * n / (dom_ms * 1e-3) / 1e9
