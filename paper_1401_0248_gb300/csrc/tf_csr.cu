@@ -74,11 +74,11 @@ __global__ void csr_prepare(const int64_t* __restrict__ off, int64_t nseg, int64
     }
 }
 
-// binary64 data at U = 1 (not wide): registers for 3 blocks of 512 threads,
-// the occupancy of the single-vector kernel, which its integer-pipe
-// arithmetic needs (the compiler fits these without spilling)
+// binary64 data (not wide): registers for 3 blocks of 512 threads at U = 1
+// (the occupancy of the single-vector kernel), 2 at U = 2; the integer-pipe
+// arithmetic needs the warps, and the compiler fits these without spilling
 template <typename T, int VAR, bool DOT, int U>
-__global__ void __launch_bounds__(512, (sizeof(T) == 8 && U == 1 && VAR != WIDE) ? 3 : 1)
+__global__ void __launch_bounds__(512, (sizeof(T) == 8 && VAR != WIDE) ? (U == 1 ? 3 : (U == 2 ? 2 : 1)) : 1)
 csr_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* __restrict__ off,
            int64_t nseg, void* __restrict__ out, unsigned char* __restrict__ ws,
            size_t cnt_bytes, const int64_t* __restrict__ tile_seg, int64_t tile, int aligned,
