@@ -429,7 +429,7 @@ tf_status tf_tune(tf_op op, int batched, tf_dtype dtype, tf_variant variant, con
     const int V = dtype == 0 ? 4 : 2;
     for (int block : {128, 256, 512})
         for (int unroll : {1, 2, 4})
-            for (int bps : {1, 2, 4, 8}) {
+            for (int bps : {1, 2, 3, 4, 5, 6, 8}) {
                 if (block * bps > 2048) continue;
                 if (!batched) {
                     cands.push_back({block, unroll, bps, 0});

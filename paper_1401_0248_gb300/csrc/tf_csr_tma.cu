@@ -96,6 +96,7 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
         t = __shfl_sync(FULL, t, 0);
         if (lane == 0) tn_raw = atomicAdd(&hdr->tile_next, 1ull);
         int64_t tn = -1;                          // the next tile, once read
+        int64_t sn = -1;                          // its first segment, loaded when tn is read
         int64_t pt = (int64_t)t, pc = 0, pnc = (int64_t)t < ntiles ? nchunks((int64_t)t) : 0;
         uint32_t issued = 0, freed = 0, kbase = 0;
         bool failed = false;
@@ -106,7 +107,10 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
             while (issued < freed + kStages) {
                 if (pc >= pnc) {
                     if (pt != (int64_t)t) break;            // one tile ahead at most
-                    if (tn < 0) tn = (int64_t)__shfl_sync(FULL, tn_raw, 0);
+                    if (tn < 0) {
+                        tn = (int64_t)__shfl_sync(FULL, tn_raw, 0);
+                        if (tn < ntiles) sn = __ldg(tile_seg + tn);   // used at the tile's start
+                    }
                     if (tn >= ntiles) break;
                     pt = tn;
                     pc = 0;
@@ -137,7 +141,8 @@ csr_tma_kernel(const T* __restrict__ x, const T* __restrict__ y, const int64_t* 
             // read from global memory)
             const int vrel = (int)max((int64_t)0, min(vend - tlo, tile));
             top_up();
-            int64_t s = __ldg(tile_seg + t);
+            int64_t s = sn >= 0 ? sn : __ldg(tile_seg + t);
+            sn = -1;
             int64_t a = __ldg(off + s), b = __ldg(off + s + 1);
             int64_t bn = __ldg(off + min(s + 2, nseg));   // the next segment's end, loaded ahead
             int cur = -1;                          // chunk of the tile being read
