@@ -794,8 +794,9 @@ def run_small(dev, stream, reps=20):
 def run_batched(args, dev, stream):
     """The ragged-batch configuration beside the step: 16,384 binary32 CSR
     segments with log-uniform lengths in [16, 2^18] (uniform [-1, 1) data),
-    each call one offsets check plus one persistent launch, replayed from a
-    CUDA graph; the twofold binary64 forms of the same layout beside it."""
+    each call an offsets check, one persistent launch and the merge of the
+    segments over several tiles, replayed from a CUDA graph; the twofold
+    binary64 forms of the same layout beside it."""
     import torch
     from paper_1401_0248_gb300 import inputs as I
     from paper_1401_0248_gb300 import twofold as tf
