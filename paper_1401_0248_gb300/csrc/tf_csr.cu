@@ -12,14 +12,14 @@
 // chain's bits unchanged (Kahan chains skip them), so the chain assignment is
 // the documented one.  A segment inside one tile is written directly.  The
 // pieces of a segment over 2..32 tiles are stored, and a merge kernel
-// launched after the reduction merges them (one thread per segment, the
-// kernel boundary ordering the stores before the loads: no atomics on the
-// streaming warps); over more than 32 tiles they merge by a pairwise tree in
-// tile order, each merge done by the warp that completes the second of its
-// two children (arrival counters, no waiting).  Which warp reduces which
-// tile never changes a bit.  A first small kernel checks the offsets, clears
-// the counters, writes the empty segments and records the segment holding
-// each tile's first element.
+// launched after the reduction merges them (one thread per segment; its wait
+// for the reduction grid to complete orders the stores before its loads: no
+// atomics on the streaming warps); over more than 32 tiles they merge by a
+// pairwise tree in tile order, each merge done by the warp that completes the
+// second of its two children (arrival counters, no waiting).  Which warp
+// reduces which tile never changes a bit.  A first small kernel checks the
+// offsets, clears the counters, writes the empty segments and records the
+// segment holding each tile's first element.
 #include "tf_csr.cuh"
 
 namespace tf {

@@ -153,9 +153,10 @@ __device__ __forceinline__ void piece_finish(typename Acc<T, VAR>::type (&cs)[C]
     const int64_t w0 = a / tile, k = (b - 1) / tile - w0 + 1;
     G gv = (G)pv, ge = (G)pe;                   // the node [st, st + w) in registers
     if (k <= 32) {
-        // plain stores, which the kernel boundary orders before csr_merge's
-        // loads; the warp of the first piece also records k in the word of
-        // slot 2*w0 + 1 (the tree below counts arrivals in even slots only)
+        // plain stores, which csr_merge's wait for this grid to complete
+        // orders before its loads; the warp of the first piece records k in
+        // the word of slot 2*w0 + 1 (the tree below counts arrivals in even
+        // slots only)
         if (lane == kPubLane) {
             G* mine = pieces + 2 * piece_slot(w0, t - w0);
             mine[0] = gv;
