@@ -532,6 +532,33 @@ def test_csr_segment_over_thousands_of_tiles(dt):
                         before["blocks_per_sm"], before["tile"])
 
 
+@pytest.mark.parametrize("tile", [1024, 4096])
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("variant", ["fast", "rigorous", "kahan", "wide"])
+def test_csr_pieces_at_each_power_of_two(dt, variant, tile):
+    """Segments over exactly k tiles for k = 2..5, 8, 9, 16, 17, 31, 32 and 33
+    (the merge kernel's butterfly over 2, 4, 8, 16 and 32 lanes on both sides
+    of each power of two, and the first count that takes the arrival tree),
+    each starting on a tile edge or inside a tile; tiles of 1024 run the
+    register kernel, tiles of 4096 the shared-memory ring where it fits."""
+    L = []
+    for k in (2, 3, 4, 5, 8, 9, 16, 17, 31, 32, 33):
+        L += [tile * k, 3, tile * (k - 1) - 3 + 1]     # k tiles from an edge; then k tiles from inside
+        L.append(tile - ((sum(L)) % tile) if sum(L) % tile else 0)   # back to a tile edge
+    off_h = I.csr_offsets(L)
+    n = int(off_h[-1])
+    x = I.normal(n, dt, seed=33, device=DEV)
+    y = I.normal(n, dt, seed=33, stream=6, device=DEV)
+    for op in ("sum", "dot"):
+        before = tf.plan_get(op, True, TD[dt], variant)
+        try:
+            tf.plan_set(op, True, TD[dt], variant, 128, 1, 2, tile)
+            check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
+        finally:
+            tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
+                        before["blocks_per_sm"], before["tile"])
+
+
 @pytest.mark.parametrize("dt", ["f32", "f64"])
 @pytest.mark.parametrize("unroll,block", [(1, 128), (2, 512), (4, 256)])
 def test_csr_staged_ring_edges(dt, unroll, block):
