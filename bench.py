@@ -42,6 +42,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -86,14 +87,19 @@ FALLBACK_DFMA_GOPS = 626.0   # binary64 fused multiply-adds/s (2/clk/SM at 2.07 
 
 
 def kernel_sources_hash(files=("tf_device.cuh", "tf_flat.cu")):
-    """Hash of the sources a kernel is built from (the single-vector kernel by
-    default); a recorded ncu traffic figure is used only while it matches."""
+    """Hash of the code a kernel is built from (the single-vector kernel by
+    default), comments and blank space left out so that only a change of code
+    counts; a recorded ncu traffic figure is used only while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1401_0248_gb300", "csrc")
     for f in files:
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode())
-            h.update(fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(" ".join(line.split()) for line in src.splitlines() if line.strip())
+        h.update(f.encode())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -461,16 +461,16 @@ template <int VAR> constexpr bool twofold_v = (VAR != PLAIN && VAR != WIDE);
 // the per-item step after the product: literal dots step like the sums
 template <int VAR> constexpr int step_v = VAR == FAST_LIT ? FAST : (VAR == RIG_LIT ? RIGOROUS : VAR);
 
-// One item into one chain (s, e).  Sums: y = x.  Dots: y = RN(x*y) and, for
-// the twofold variants, ep = its TwoProduct error.
-//   fast (Example 1):     t = s + y; c = (t - s) - y; e = e - c; s = t
-//                         dot: e = e + (ep - c)
-//   rigorous (Example 3): t = s + y; yt = t - s; dy = y - yt;
-//                         ds = s - (t - yt); e = e + (ds + dy); s = t
-//                         dot: e = e + ((ds + dy) + ep)
-//   plain:                s = s + y
-//   wide:                 S = S + y in binary64 (binary32 products are exact
-//                         in binary64)
+// One item into one chain (s, e).  Sums: the item is x.  Dots: the item is
+// RN(x*y) and, for the twofold variants, ep is its TwoProduct error.
+//   fast (Example 1):     the chain value and the item go through FAST-TWO-SUM
+//                         (Theorem 1); the sum becomes the chain value and the
+//                         transform's error is added to e (dots: the error and
+//                         ep are added together first, then to e)
+//   rigorous (Example 3): the same with TWO-SUM (Theorem 2)
+//   plain:                the item is added to the chain value
+//   wide:                 the item is added to a binary64 accumulator
+//                         (binary32 products are exact in binary64)
 // `one` is a runtime 1.0 (see dadd): the binary64 sums and twofold dots and
 // the binary64 accumulator of binary32 data ('wide') issue their adds as DFMA
 // (the plain binary64 dot rounds its product first, by a multiply).
@@ -501,8 +501,10 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
         // binary64: the error-free transforms take one binary64 add (or none
         // for the product) plus integer work; the bits are those of the
         // binary64 operation sequences of Examples 1-3.  The fast step is
-        // FAST-TWO-SUM(s, p) followed by e = e + y, since c = (t - s) - p = -y;
-        // Kahan's step is FAST-TWO-SUM(s, p + e): e <- (p + e) - (t - s).
+        // FAST-TWO-SUM of the chain value and the item, its error added to e
+        // (Example 1's compensation term is that error negated); Kahan's step
+        // is FAST-TWO-SUM of the chain value and the item plus e, whose error
+        // becomes the new e.
         double p, ep = 0.0;
         if constexpr (TPROD) {
             if (!two_product_i64(a, b, p, ep)) { const double2 r = two_product_slow(a, b); p = r.x; ep = r.y; }
@@ -530,7 +532,8 @@ __device__ __forceinline__ void feed(A& s, A& e, T a, T b, double one = 1.0) {
         T p, ep = T(0);
         if constexpr (TPROD) two_product(a, b, p, ep); else p = DOT ? mul_rn(a, b) : a;
         if constexpr (STEP == KAHAN) {
-            // Example 2 with e = -c: y' = y - c = y + e, c = (t - s) - y' = -e
+            // Example 2 with e holding the negated compensation term: the item
+            // plus e joins the chain value, and the new e is what that sum lost
             const T yk = add_rn(p, e);
             const T t = add_rn(s, yk);
             e = sub_rn(yk, sub_rn(t, s));
