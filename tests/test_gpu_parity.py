@@ -559,6 +559,42 @@ def test_csr_pieces_at_each_power_of_two(dt, variant, tile):
                         before["blocks_per_sm"], before["tile"])
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_csr_random_layouts(seed):
+    """Random mixes of empty, short, about-one-tile and multi-tile segments
+    (up to 40 tiles, so both the merge kernel and the arrival tree run), at a
+    random tile size and launch shape; every pair bit for bit against the
+    replay."""
+    rng = np.random.default_rng(100 + seed)
+    tile = int(rng.choice([1024, 2048, 4096]))
+    kinds = rng.integers(0, 4, size=300)
+    L = []
+    for k in kinds:
+        if k == 0:
+            L.append(int(rng.integers(0, 3)))                       # empty or tiny
+        elif k == 1:
+            L.append(int(rng.integers(1, 200)))                     # short
+        elif k == 2:
+            L.append(int(tile + rng.integers(-64, 65)))             # about one tile
+        else:
+            L.append(int(rng.integers(2, 40) * tile + rng.integers(-500, 500)))   # many tiles
+    off_h = I.csr_offsets(L)
+    n = int(off_h[-1])
+    block = int(rng.choice([128, 256, 512]))
+    bps = int(rng.choice([1, 2, 3]))
+    for dt in ("f32", "f64"):
+        x = I.normal(n, dt, seed=200 + seed, device=DEV)
+        y = I.normal(n, dt, seed=200 + seed, stream=7, device=DEV)
+        for op, variant in (("sum", "fast"), ("dot", "rigorous")):
+            before = tf.plan_get(op, True, TD[dt], variant)
+            try:
+                tf.plan_set(op, True, TD[dt], variant, block, 1, bps, tile)
+                check_csr(op, variant, dt, x, y if op == "dot" else None, off_h)
+            finally:
+                tf.plan_set(op, True, TD[dt], variant, before["block"], before["unroll"],
+                            before["blocks_per_sm"], before["tile"])
+
+
 @pytest.mark.parametrize("dt", ["f32", "f64"])
 @pytest.mark.parametrize("unroll,block", [(1, 128), (2, 512), (4, 256)])
 def test_csr_staged_ring_edges(dt, unroll, block):
